@@ -1,0 +1,13 @@
+"""FP64 CPU oracle of the displaced-track Hough transform -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the entry point's smoke check and the benchmark's CPU-baseline leg may
+import this package.  It shares no code with the CUDA library and never reads anything
+the CUDA path produced as an input.
+
+  enumerate_batch  -- the C definition (trk_oracle.c): every triplet of every listed
+                      layer triple, FP64 helix fit, binning, edge-ambiguity flags;
+  reconstruct      -- votes, peak rule and hit assignment (reconstruct.py, numpy).
+"""
+from .core import OracleSetup, enumerate_batch, fit_list, max_threads  # noqa: F401
+from .reconstruct import (histogram, neighbour_offsets, peaks, assign_hits,  # noqa: F401
+                          reconstruct)

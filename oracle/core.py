@@ -1,0 +1,161 @@
+"""ctypes front of the C oracle (trk_oracle.c).  Test infrastructure only."""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(_build.build())
+        lib.orc_run.restype = C.c_int
+        lib.orc_run.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p,
+                                C.c_int32, C.c_void_p]
+        lib.orc_result_free.argtypes = [C.c_void_p]
+        lib.orc_fit.restype = C.c_int
+        lib.orc_fit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]
+        lib.orc_fit_list.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.orc_max_threads.restype = C.c_int32
+        _lib = lib
+    return _lib
+
+
+class _Setup(C.Structure):
+    _fields_ = [("b_tesla", C.c_double), ("n_layers", C.c_int32), ("n_triples", C.c_int32),
+                ("triples", C.c_void_p), ("lo", C.c_double * 5), ("hi", C.c_double * 5),
+                ("n", C.c_int32 * 5), ("periodic", C.c_int32), ("eps_rel", C.c_double)]
+
+
+class _Result(C.Structure):
+    _fields_ = [("n_acc", C.c_int64), ("acc_event", C.c_void_p), ("acc_ijk", C.c_void_p),
+                ("acc_bin", C.c_void_p), ("acc_amb", C.c_void_p), ("acc_par", C.c_void_p),
+                ("n_near", C.c_int64), ("near_event", C.c_void_p), ("near_ijk", C.c_void_p),
+                ("n_triplets", C.c_int64), ("n_degenerate", C.c_int64)]
+
+
+@dataclass
+class OracleSetup:
+    """Geometry and binning as the oracle reads them (from a workload description)."""
+    b_tesla: float
+    n_layers: int
+    triples: np.ndarray          # (T, 3) int32
+    lo: np.ndarray               # (5,) float64
+    hi: np.ndarray
+    n: np.ndarray                # (5,) int64
+    periodic: np.ndarray         # (5,) bool
+    threshold: int
+    eps_rel: float = 1e-5
+
+    @classmethod
+    def from_workload(cls, cfg: dict, **over) -> "OracleSetup":
+        g, b = cfg["geometry"], cfg["binning"]
+        kw = dict(b_tesla=float(g["b_tesla"]), n_layers=len(g["radius"]),
+                  triples=np.asarray(g["triples"], dtype=np.int32).reshape(-1, 3),
+                  lo=np.asarray(b["lo"], dtype=np.float64), hi=np.asarray(b["hi"], dtype=np.float64),
+                  n=np.asarray(b["n"], dtype=np.int64), periodic=np.asarray(b["periodic"], dtype=bool),
+                  threshold=int(b["threshold"]))
+        kw.update(over)
+        return cls(**kw)
+
+    @property
+    def n_bins(self) -> int:
+        return int(np.prod(self.n))
+
+    def _c(self):
+        tri = np.ascontiguousarray(self.triples, dtype=np.int32)
+        s = _Setup()
+        s.b_tesla = self.b_tesla
+        s.n_layers = self.n_layers
+        s.n_triples = len(tri)
+        s.triples = tri.ctypes.data
+        for k in range(5):
+            s.lo[k] = float(self.lo[k])
+            s.hi[k] = float(self.hi[k])
+            s.n[k] = int(self.n[k])
+        s.periodic = int(sum(1 << k for k in range(5) if self.periodic[k]))
+        s.eps_rel = self.eps_rel
+        return s, tri
+
+
+def _hits_struct(xyz: np.ndarray, layer: np.ndarray) -> np.ndarray:
+    h = np.empty((len(xyz), 4), dtype=np.float32)
+    h[:, :3] = np.asarray(xyz, dtype=np.float32)
+    h[:, 3] = np.asarray(layer, dtype=np.int32).view(np.float32)
+    return np.ascontiguousarray(h)
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+def enumerate_batch(xyz, layer, offsets, setup: OracleSetup, n_threads: int = 0) -> dict:
+    """Every triplet of the definition; accepted ones with bins, ambiguity, parameters."""
+    lib = _load()
+    hits = _hits_struct(xyz, layer)
+    offs = np.ascontiguousarray(offsets, dtype=np.int64)
+    s, tri = setup._c()
+    res = _Result()
+    rc = lib.orc_run(hits.ctypes.data, C.c_int64(len(hits)), offs.ctypes.data,
+                     C.c_int32(len(offs) - 1), C.byref(s), C.c_int32(n_threads), C.byref(res))
+    if rc != 0:
+        raise ValueError("oracle: invalid input (layer id out of range or bad offsets)")
+    try:
+        na, nn = res.n_acc, res.n_near
+
+        def arr(ptr, dtype, count):
+            if count == 0:
+                return np.zeros(0, dtype=dtype)
+            buf = (C.c_char * (count * np.dtype(dtype).itemsize)).from_address(ptr)
+            return np.frombuffer(buf, dtype=dtype).copy()
+        out = dict(
+            event=arr(res.acc_event, np.int32, na),
+            ijk=arr(res.acc_ijk, np.int32, 3 * na).reshape(-1, 3),
+            bin=arr(res.acc_bin, np.uint64, na).astype(np.int64),
+            amb=arr(res.acc_amb, np.uint8, na).astype(bool),
+            par=arr(res.acc_par, np.float64, 5 * na).reshape(-1, 5),
+            near_event=arr(res.near_event, np.int32, nn),
+            near_ijk=arr(res.near_ijk, np.int32, 3 * nn).reshape(-1, 3),
+            n_triplets=int(res.n_triplets),
+            n_degenerate=int(res.n_degenerate),
+            n_events=len(offs) - 1,
+        )
+    finally:
+        lib.orc_result_free(C.byref(res))
+    return out
+
+
+def fit_list(xyz, layer, ijk, setup: OracleSetup, n_threads: int = 0) -> dict:
+    """Fit and bin explicit triplets (global input hit indices)."""
+    lib = _load()
+    hits = _hits_struct(xyz, layer)
+    ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    n = len(ijk)
+    par = np.zeros((n, 5), dtype=np.float64)
+    binv = np.zeros(n, dtype=np.uint64)
+    status = np.zeros(n, dtype=np.int32)
+    amb = np.zeros(n, dtype=np.uint8)
+    s, tri = setup._c()
+    lib.orc_fit_list(hits.ctypes.data, ijk.ctypes.data, C.c_int64(n), C.byref(s),
+                     C.c_int32(n_threads), par.ctypes.data, binv.ctypes.data,
+                     status.ctypes.data, amb.ctypes.data)
+    return dict(par=par, bin=binv.astype(np.int64), status=status, amb=amb.astype(bool))
+
+
+def fit_one(p1, p2, p3, b_tesla: float):
+    """Helix parameters of one triplet (FP64), or None if degenerate."""
+    lib = _load()
+    a = np.ascontiguousarray(p1, dtype=np.float64)
+    b = np.ascontiguousarray(p2, dtype=np.float64)
+    c = np.ascontiguousarray(p3, dtype=np.float64)
+    par = np.zeros(5, dtype=np.float64)
+    rc = lib.orc_fit(a.ctypes.data, b.ctypes.data, c.ctypes.data, C.c_double(b_tesla),
+                     par.ctypes.data)
+    return None if rc != 0 else par

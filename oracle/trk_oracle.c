@@ -1,0 +1,438 @@
+/*
+ * FP64 CPU oracle of the displaced-track Hough transform.  TEST INFRASTRUCTURE ONLY:
+ * it is linked by the tests, by the entry point's smoke check and by the benchmark's CPU
+ * baseline leg, and by nothing on the product path.  It shares no code, header or
+ * constant with the CUDA library.
+ *
+ * What it computes (plain definition, no blocking, no pruning, no reordering):
+ *   for every event, every listed layer triple (a, b, c), every hit i of layer a, j of
+ *   layer b, k of layer c (input order), in double precision from the float32 hits:
+ *     1. the circle through the three transverse points, its signed curvature and the
+ *        helix perigee parameters (phi0, q/pT, d0) about the coordinate origin
+ *        (no beam-spot constraint), the arc lengths s_k from the perigee and the
+ *        unweighted least-squares line z = z0 + s cot(theta) over the three (s_k, z_k);
+ *     2. the five bin indices; the triplet is accepted iff all five parameters lie in
+ *        range, and then votes once into bin (phi0, q/pT, d0, cot, z0), row-major;
+ *     3. an edge-ambiguity flag: some parameter lies within eps of a bin edge or range
+ *        limit, eps = eps_rel * max(|p|, half-range).
+ *
+ * Paper: Sec. 7 and Fig. 3 (each hit set maps to many parameter points, votes are
+ * accumulated, peaks are tracks); Sec. 8 (curved features need more parameters,
+ * circles by centre and radius; curved displaced tracks need a space beyond the
+ * two-parameter interaction-point-constrained one).  The helix parameterisation,
+ * the sign conventions, the arc length and the longitudinal fit are not given in the
+ * paper; they are the stated readings:
+ *   - pT = K B R, K = 0.299792458e-2 GeV/(T cm); positive charges turn clockwise
+ *     seen from +z, so q = -sign(D) with D = (p2-p1) x (p3-p1), q/pT = -sign(D)/(K B R);
+ *   - centre c = p1 + (v_y|u|^2 - u_y|v|^2, u_x|v|^2 - v_x|u|^2) / (2D), R = |c - p1|;
+ *   - perigee P = c (1 - R/|c|); phi0 = direction of motion at P, in [-pi, pi);
+ *     d0 = -P_x sin(phi0) + P_y cos(phi0); |c| - R is evaluated as
+ *     (|c|^2 - R^2)/(|c| + R) with |c|^2 - R^2 = |p1|^2 + 2 p1.(c - p1) (an identity,
+ *     used because the direct difference of two large numbers loses all digits);
+ *   - D == 0: straight line through p1 and p3, q/pT = 0, P the foot of the normal;
+ *   - s_k = 2R asin(|p_k - P| / (2R)) (|p_k - P| on a straight line);
+ *   - bins: idx = floor((p - lo) / ((hi - lo)/n)), accepted iff lo <= p < hi; a periodic
+ *     dimension is wrapped into [lo, hi) first.
+ * Degenerate triplets (circle centred on the origin, or three equal arc lengths) have
+ * no perigee or no slope and are rejected and counted.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_K 0.299792458e-2
+
+typedef struct {
+    float x, y, z;
+    int32_t layer;
+} orc_hit;
+
+typedef struct {
+    double b_tesla;
+    int32_t n_layers;
+    int32_t n_triples;
+    const int32_t *triples; /* n_triples x 3 layer ids */
+    double lo[5], hi[5];
+    int32_t n[5];
+    int32_t periodic;       /* bit k set: dimension k is periodic */
+    double eps_rel;
+} orc_setup;
+
+typedef struct {
+    int64_t n_acc;          /* accepted triplets */
+    int32_t *acc_event;     /* [n_acc] */
+    int32_t *acc_ijk;       /* [n_acc * 3] input hit indices (global) */
+    uint64_t *acc_bin;      /* [n_acc] row-major bin inside the event's histogram */
+    uint8_t *acc_amb;       /* [n_acc] edge-ambiguous */
+    double *acc_par;        /* [n_acc * 5] */
+    int64_t n_near;         /* rejected, but every out-of-range parameter within eps */
+    int32_t *near_event;
+    int32_t *near_ijk;
+    int64_t n_triplets;     /* sum over events and triples of |La||Lb||Lc| */
+    int64_t n_degenerate;
+} orc_result;
+
+enum { ORC_OK = 0, ORC_DEGENERATE = 1 };
+
+/* Helix of the triplet.  Returns ORC_OK and par = (phi0, q/pT, d0, cot, z0), or
+ * ORC_DEGENERATE. */
+int orc_fit(const double *p1, const double *p2, const double *p3, double b_tesla,
+            double *par)
+{
+    const double ux = p2[0] - p1[0], uy = p2[1] - p1[1];
+    const double vx = p3[0] - p1[0], vy = p3[1] - p1[1];
+    const double D = ux * vy - uy * vx;
+    double phi0, qopt, d0, px, py, R;
+    int straight = (D == 0.0);
+    if (!straight) {
+        const double uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
+        const double cpx = (vy * uu - uy * vv) / (2.0 * D);
+        const double cpy = (ux * vv - vx * uu) / (2.0 * D);
+        const double cx = p1[0] + cpx, cy = p1[1] + cpy;
+        const double sgn = D > 0.0 ? 1.0 : -1.0;
+        R = sqrt(cpx * cpx + cpy * cpy);
+        qopt = -sgn / (ORC_K * b_tesla * R);
+        const double cn = sqrt(cx * cx + cy * cy);
+        if (cn == 0.0)
+            return ORC_DEGENERATE;
+        const double power = (p1[0] * p1[0] + p1[1] * p1[1]) + 2.0 * (p1[0] * cpx + p1[1] * cpy);
+        const double cn_minus_r = power / (cn + R);
+        px = cx * (cn_minus_r / cn);
+        py = cy * (cn_minus_r / cn);
+        /* direction of motion at P: counter-clockwise (D > 0) is z x (P - c), and
+         * P - c points from c towards the origin, so the tangent is sgn (c_y, -c_x)/|c| */
+        phi0 = atan2(-sgn * cx, sgn * cy);
+        d0 = -px * sin(phi0) + py * cos(phi0);
+    } else {
+        const double vn = sqrt(vx * vx + vy * vy);
+        if (vn == 0.0)
+            return ORC_DEGENERATE;
+        const double tx = vx / vn, ty = vy / vn;
+        const double along = p1[0] * tx + p1[1] * ty;
+        px = p1[0] - along * tx;
+        py = p1[1] - along * ty;
+        phi0 = atan2(vy, vx);
+        d0 = -px * sin(phi0) + py * cos(phi0);
+        qopt = 0.0;
+        R = INFINITY;
+    }
+    const double *pk[3] = {p1, p2, p3};
+    double s[3];
+    for (int k = 0; k < 3; ++k) {
+        const double dx = pk[k][0] - px, dy = pk[k][1] - py;
+        const double chord = sqrt(dx * dx + dy * dy);
+        if (straight) {
+            s[k] = chord;
+        } else {
+            double a = chord / (2.0 * R);
+            if (a > 1.0)
+                a = 1.0;
+            s[k] = 2.0 * R * asin(a);
+        }
+    }
+    const double sbar = (s[0] + s[1] + s[2]) / 3.0;
+    const double zbar = (p1[2] + p2[2] + p3[2]) / 3.0;
+    double sss = 0.0, ssz = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        sss += (s[k] - sbar) * (s[k] - sbar);
+        ssz += (s[k] - sbar) * (pk[k][2] - zbar);
+    }
+    if (sss == 0.0)
+        return ORC_DEGENERATE;
+    const double cot = ssz / sss;
+    const double z0 = zbar - cot * sbar;
+    par[0] = phi0;
+    par[1] = qopt;
+    par[2] = d0;
+    par[3] = cot;
+    par[4] = z0;
+    return ORC_OK;
+}
+
+/* Bin the parameters.  Returns 1 if accepted (all in range) with *bin set; sets *amb if
+ * some parameter is within eps of an edge or range limit; *near = rejected but every
+ * out-of-range parameter is within eps of its range limit. */
+int orc_bin(const orc_setup *s, const double *par_in, uint64_t *bin, int *amb, int *near)
+{
+    int inside = 1, all_close = 1;
+    uint64_t lin = 0;
+    *amb = 0;
+    for (int k = 0; k < 5; ++k) {
+        double p = par_in[k];
+        const double lo = s->lo[k], hi = s->hi[k];
+        const double w = (hi - lo) / (double)s->n[k];
+        if ((s->periodic >> k) & 1) {
+            const double period = hi - lo;
+            while (p >= hi)
+                p -= period;
+            while (p < lo)
+                p += period;
+        }
+        const double half = 0.5 * (hi - lo);
+        const double eps = s->eps_rel * (fabs(p) > half ? fabs(p) : half);
+        int64_t idx;
+        if (p < lo || p >= hi) {
+            inside = 0;
+            const double d = p < lo ? lo - p : p - hi;
+            if (d > eps)
+                all_close = 0;
+            else
+                *amb = 1;
+            idx = 0;
+        } else {
+            const double t = (p - lo) / w;
+            idx = (int64_t)floor(t);
+            if (idx >= s->n[k])
+                idx = s->n[k] - 1;
+            const double below = t - floor(t), above = ceil(t) - t;
+            const double dedge = (below < above ? below : above) * w;
+            if (dedge <= eps)
+                *amb = 1;
+        }
+        lin = lin * (uint64_t)s->n[k] + (uint64_t)idx;
+    }
+    *bin = lin;
+    *near = (!inside) && all_close;
+    return inside;
+}
+
+typedef struct {
+    int64_t n, cap;
+    int32_t *ijk;
+    uint64_t *bin;
+    uint8_t *amb;
+    double *par;
+    int64_t nn, ncap;
+    int32_t *near_ijk;
+    int64_t n_degenerate;
+} unit_buf;
+
+static void ub_push_acc(unit_buf *b, int32_t i, int32_t j, int32_t k, uint64_t bin, int amb,
+                        const double *par)
+{
+    if (b->n == b->cap) {
+        b->cap = b->cap ? 2 * b->cap : 64;
+        b->ijk = realloc(b->ijk, (size_t)b->cap * 3 * sizeof(int32_t));
+        b->bin = realloc(b->bin, (size_t)b->cap * sizeof(uint64_t));
+        b->amb = realloc(b->amb, (size_t)b->cap);
+        b->par = realloc(b->par, (size_t)b->cap * 5 * sizeof(double));
+    }
+    b->ijk[3 * b->n] = i;
+    b->ijk[3 * b->n + 1] = j;
+    b->ijk[3 * b->n + 2] = k;
+    b->bin[b->n] = bin;
+    b->amb[b->n] = (uint8_t)amb;
+    memcpy(b->par + 5 * b->n, par, 5 * sizeof(double));
+    b->n++;
+}
+
+static void ub_push_near(unit_buf *b, int32_t i, int32_t j, int32_t k)
+{
+    if (b->nn == b->ncap) {
+        b->ncap = b->ncap ? 2 * b->ncap : 16;
+        b->near_ijk = realloc(b->near_ijk, (size_t)b->ncap * 3 * sizeof(int32_t));
+    }
+    b->near_ijk[3 * b->nn] = i;
+    b->near_ijk[3 * b->nn + 1] = j;
+    b->near_ijk[3 * b->nn + 2] = k;
+    b->nn++;
+}
+
+/* Run the whole definition over a batch of events.  Output order: event, layer triple
+ * (list order), i, j, k (input order within each layer) -- independent of the thread
+ * count.  Returns 0, or -1 on invalid input (layer id out of range, bad offsets). */
+int orc_run(const orc_hit *hits, int64_t n_hits, const int64_t *offsets, int32_t n_events,
+            const orc_setup *s, int32_t n_threads, orc_result *res)
+{
+    memset(res, 0, sizeof(*res));
+    if (offsets[0] != 0 || offsets[n_events] != n_hits)
+        return -1;
+    for (int32_t e = 0; e < n_events; ++e)
+        if (offsets[e + 1] < offsets[e])
+            return -1;
+    for (int64_t h = 0; h < n_hits; ++h)
+        if (hits[h].layer < 0 || hits[h].layer >= s->n_layers)
+            return -1;
+
+    /* per event, per layer: the input indices of the layer's hits, in input order */
+    const int L = s->n_layers;
+    int64_t *lay_off = calloc((size_t)n_events * (L + 1), sizeof(int64_t));
+    int32_t *lay_idx = malloc((size_t)(n_hits > 0 ? n_hits : 1) * sizeof(int32_t));
+    for (int32_t e = 0; e < n_events; ++e) {
+        int64_t *lo = lay_off + (size_t)e * (L + 1);
+        for (int64_t h = offsets[e]; h < offsets[e + 1]; ++h)
+            lo[hits[h].layer + 1]++;
+        lo[0] = offsets[e];
+        for (int l = 0; l < L; ++l)
+            lo[l + 1] += lo[l];
+        int64_t *fill = malloc((size_t)L * sizeof(int64_t));
+        for (int l = 0; l < L; ++l)
+            fill[l] = lo[l];
+        for (int64_t h = offsets[e]; h < offsets[e + 1]; ++h)
+            lay_idx[fill[hits[h].layer]++] = (int32_t)h;
+        free(fill);
+    }
+
+    /* work units: (event, triple, inner hit) in output order */
+    int64_t n_units = 0;
+    for (int32_t e = 0; e < n_events; ++e)
+        for (int t = 0; t < s->n_triples; ++t) {
+            const int a = s->triples[3 * t], b = s->triples[3 * t + 1], c = s->triples[3 * t + 2];
+            const int64_t *lo = lay_off + (size_t)e * (L + 1);
+            const int64_t na = lo[a + 1] - lo[a], nb = lo[b + 1] - lo[b], nc = lo[c + 1] - lo[c];
+            n_units += na;
+            res->n_triplets += na * nb * nc;
+        }
+    int32_t *u_event = malloc((size_t)(n_units ? n_units : 1) * sizeof(int32_t));
+    int32_t *u_triple = malloc((size_t)(n_units ? n_units : 1) * sizeof(int32_t));
+    int64_t *u_i = malloc((size_t)(n_units ? n_units : 1) * sizeof(int64_t));
+    {
+        int64_t u = 0;
+        for (int32_t e = 0; e < n_events; ++e)
+            for (int t = 0; t < s->n_triples; ++t) {
+                const int a = s->triples[3 * t];
+                const int64_t *lo = lay_off + (size_t)e * (L + 1);
+                for (int64_t i = lo[a]; i < lo[a + 1]; ++i) {
+                    u_event[u] = e;
+                    u_triple[u] = t;
+                    u_i[u] = i;
+                    ++u;
+                }
+            }
+    }
+    unit_buf *ub = calloc((size_t)(n_units ? n_units : 1), sizeof(unit_buf));
+
+#ifdef _OPENMP
+    if (n_threads > 0)
+        omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t u = 0; u < n_units; ++u) {
+        const int32_t e = u_event[u];
+        const int t = u_triple[u];
+        const int b = s->triples[3 * t + 1], c = s->triples[3 * t + 2];
+        const int64_t *lo = lay_off + (size_t)e * (L + 1);
+        const int32_t hi_ = lay_idx[u_i[u]];
+        const double p1[3] = {hits[hi_].x, hits[hi_].y, hits[hi_].z};
+        unit_buf *buf = ub + u;
+        for (int64_t jj = lo[b]; jj < lo[b + 1]; ++jj) {
+            const int32_t hj = lay_idx[jj];
+            const double p2[3] = {hits[hj].x, hits[hj].y, hits[hj].z};
+            for (int64_t kk = lo[c]; kk < lo[c + 1]; ++kk) {
+                const int32_t hk = lay_idx[kk];
+                const double p3[3] = {hits[hk].x, hits[hk].y, hits[hk].z};
+                double par[5];
+                if (orc_fit(p1, p2, p3, s->b_tesla, par) != ORC_OK) {
+                    buf->n_degenerate++;
+                    continue;
+                }
+                uint64_t bin;
+                int amb, near;
+                if (orc_bin(s, par, &bin, &amb, &near))
+                    ub_push_acc(buf, hi_, hj, hk, bin, amb, par);
+                else if (near)
+                    ub_push_near(buf, hi_, hj, hk);
+            }
+        }
+    }
+
+    int64_t n_acc = 0, n_near = 0;
+    for (int64_t u = 0; u < n_units; ++u) {
+        n_acc += ub[u].n;
+        n_near += ub[u].nn;
+        res->n_degenerate += ub[u].n_degenerate;
+    }
+    res->n_acc = n_acc;
+    res->n_near = n_near;
+    res->acc_event = malloc((size_t)(n_acc ? n_acc : 1) * sizeof(int32_t));
+    res->acc_ijk = malloc((size_t)(n_acc ? n_acc : 1) * 3 * sizeof(int32_t));
+    res->acc_bin = malloc((size_t)(n_acc ? n_acc : 1) * sizeof(uint64_t));
+    res->acc_amb = malloc((size_t)(n_acc ? n_acc : 1));
+    res->acc_par = malloc((size_t)(n_acc ? n_acc : 1) * 5 * sizeof(double));
+    res->near_event = malloc((size_t)(n_near ? n_near : 1) * sizeof(int32_t));
+    res->near_ijk = malloc((size_t)(n_near ? n_near : 1) * 3 * sizeof(int32_t));
+    int64_t pa = 0, pn = 0;
+    for (int64_t u = 0; u < n_units; ++u) {
+        unit_buf *b = ub + u;
+        for (int64_t q = 0; q < b->n; ++q)
+            res->acc_event[pa + q] = u_event[u];
+        if (b->n) {
+            memcpy(res->acc_ijk + 3 * pa, b->ijk, (size_t)b->n * 3 * sizeof(int32_t));
+            memcpy(res->acc_bin + pa, b->bin, (size_t)b->n * sizeof(uint64_t));
+            memcpy(res->acc_amb + pa, b->amb, (size_t)b->n);
+            memcpy(res->acc_par + 5 * pa, b->par, (size_t)b->n * 5 * sizeof(double));
+        }
+        for (int64_t q = 0; q < b->nn; ++q)
+            res->near_event[pn + q] = u_event[u];
+        if (b->nn)
+            memcpy(res->near_ijk + 3 * pn, b->near_ijk, (size_t)b->nn * 3 * sizeof(int32_t));
+        pa += b->n;
+        pn += b->nn;
+        free(b->ijk);
+        free(b->bin);
+        free(b->amb);
+        free(b->par);
+        free(b->near_ijk);
+    }
+    free(ub);
+    free(u_event);
+    free(u_triple);
+    free(u_i);
+    free(lay_off);
+    free(lay_idx);
+    return 0;
+}
+
+void orc_result_free(orc_result *res)
+{
+    free(res->acc_event);
+    free(res->acc_ijk);
+    free(res->acc_bin);
+    free(res->acc_amb);
+    free(res->acc_par);
+    free(res->near_event);
+    free(res->near_ijk);
+    memset(res, 0, sizeof(*res));
+}
+
+/* Fit and bin an explicit list of triplets (input hit indices), for sampled checks at
+ * sizes the full enumeration cannot reach.  status[t]: 0 accepted, 1 rejected,
+ * 2 degenerate; amb[t] edge-ambiguous or near; par/bin filled when not degenerate. */
+void orc_fit_list(const orc_hit *hits, const int32_t *ijk, int64_t n, const orc_setup *s,
+                  int32_t n_threads, double *par, uint64_t *bin, int32_t *status,
+                  uint8_t *amb)
+{
+#ifdef _OPENMP
+    if (n_threads > 0)
+        omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t t = 0; t < n; ++t) {
+        const orc_hit *a = hits + ijk[3 * t], *b = hits + ijk[3 * t + 1], *c = hits + ijk[3 * t + 2];
+        const double p1[3] = {a->x, a->y, a->z}, p2[3] = {b->x, b->y, b->z},
+                     p3[3] = {c->x, c->y, c->z};
+        if (orc_fit(p1, p2, p3, s->b_tesla, par + 5 * t) != ORC_OK) {
+            status[t] = 2;
+            amb[t] = 0;
+            bin[t] = 0;
+            continue;
+        }
+        int am, near;
+        const int acc = orc_bin(s, par + 5 * t, bin + t, &am, &near);
+        status[t] = acc ? 0 : 1;
+        amb[t] = (uint8_t)(am || near);
+    }
+}
+
+int32_t orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
