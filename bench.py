@@ -1,0 +1,345 @@
+"""Benchmark: events/s and hit-triplets/s of the displaced-track Hough on GB300.
+
+A step is one trk_reconstruct call over one synthetic event of the 500-track 10-layer
+workload (pack, schedule, triplet fit + vote, peaks, candidates, hit assignment), with
+the inputs resident in HBM.  Each timed step is bracketed by CUDA events on the stream the
+library runs on, and the L2 is flushed (a 512 MB write) between steps outside the timed
+window.  `e2e` runs the same steps through trk_reconstruct_host from pinned host memory
+(hits in, candidates and hit ids out).  Under torchrun every rank runs its own replica on
+its own GPU (events are independent: no collective on the data path); the barrier and the
+max over ranks only frame the timing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "barrel10_500trk"
+# FP32 operations of the curvature prefilter evaluated for every enumerated triplet
+# (4 differences, 3 multiply + 3 fused products for D, |v|^2, |w|^2, 3 products and one
+# comparison), the unit of the vote kernel's algorithmic work.
+PREFILTER_OPS = 14
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def dist_init(n):
+    import torch
+    if n <= 1 or "RANK" not in os.environ:
+        return 0, 1, int(os.environ.get("LOCAL_RANK", 0))
+    import torch.distributed as dist
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    dist.init_process_group(backend)
+    return dist.get_rank(), dist.get_world_size(), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(cfg, batch, seconds):
+    """The FP64 oracle as it stands, on all host cores, over a bounded sample of the
+    workload: the first inner hits of every layer triple, until ~`seconds` of CPU work."""
+    import oracle
+    setup = oracle.OracleSetup.from_workload(cfg)
+    threads = oracle.max_threads()
+    # grow the number of inner hits per layer triple until the run takes long enough
+    n_inner = 8
+    while True:
+        xyz, lay, keep = _inner_subsample(batch, setup, n_inner)
+        t0 = time.perf_counter()
+        en = oracle.enumerate_batch(xyz, lay, np.array([0, len(xyz)], np.int64), setup, n_threads=threads)
+        dt = time.perf_counter() - t0
+        if dt > seconds / 4 or n_inner >= 4096:
+            break
+        n_inner *= 2
+    trip_s = en["n_triplets"] / dt
+    return trip_s, threads, ("barrel10_500trk event, every layer triple with its first %d inner-layer "
+                             "hits (%d triplets, %.1f s); events/s = triplets/s / triplets per event"
+                             % (n_inner, en["n_triplets"], dt))
+
+
+def _inner_subsample(batch, setup, n_inner):
+    """Keep only the first n_inner hits of each layer that is the inner layer of some triple
+    (all hits of the other layers): every triple's enumeration shrinks proportionally."""
+    inner = {int(t[0]) for t in setup.triples}
+    keep = []
+    for L in range(setup.n_layers):
+        idx = np.nonzero(batch.layer == L)[0]
+        keep.extend(idx[:n_inner].tolist() if L in inner else idx.tolist())
+    keep = np.array(sorted(keep))
+    return batch.xyz[keep], batch.layer[keep], keep
+
+
+def run_reference(args, cfg, batch, rank, world):
+    """The oracle arm: bounded samples of the same workload on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    setup = oracle.OracleSetup.from_workload(cfg)
+    threads = oracle.max_threads()
+    trip_event = int(batch_triplets(batch, cfg))
+    xyz, lay, _ = _inner_subsample(batch, setup, 16)
+    offs = np.array([0, len(xyz)], np.int64)
+    for _ in range(args.warmup):
+        oracle.enumerate_batch(xyz, lay, offs, setup, n_threads=threads)
+    t0 = time.perf_counter()
+    trip = 0
+    for _ in range(args.steps):
+        en = oracle.enumerate_batch(xyz, lay, offs, setup, n_threads=threads)
+        trip += en["n_triplets"]
+    dt = time.perf_counter() - t0
+    trip_s = trip / dt
+    ev_s = trip_s / trip_event
+    sample = "first 16 inner-layer hits of every layer triple of the barrel10_500trk event per step"
+    line = {"metric": "events/s", "value": ev_s, "unit": "events/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "events_per_step": 1,
+                       "triplets_per_event": trip_event},
+            "hit_triplets_per_s": trip_s,
+            "cpu_baseline": {"value": ev_s, "unit": "events/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": ev_s, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def batch_triplets(batch, cfg):
+    from paper_1305_4855_gb300 import events as ev
+    return ev.layer_triplet_count(batch, cfg["geometry"]["triples"]).sum()
+
+
+def main():
+    args = parse()
+    from paper_1305_4855_gb300 import events as ev
+    cfg = ev.load_workload(args.workload)
+    batch = ev.make_batch(cfg, n_events=1)
+    rank, world, local = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, cfg, batch, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1305_4855_gb300 import build
+    build.build()
+    from paper_1305_4855_gb300.trk import Reconstructor
+
+    n_trip = int(batch_triplets(batch, cfg))
+    rec = Reconstructor(cfg, max_events=1, max_hits=batch.n_hits, device=local,
+                        vote_capacity=1 << 28, cand_capacity=1 << 21, assign_capacity=1 << 25)
+    stream = torch.cuda.Stream()
+    hits = torch.from_numpy(batch.packed()).cuda()
+    offs = torch.from_numpy(batch.offsets).cuda()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            rc = rec.reconstruct_device(hits, offs, stream=stream)
+    stats = rec.stats()
+    res = rec.result(rc)
+    assert res.rc == 0 and int(res.status[0]) == 0, rec.error()
+
+    # ---- device-resident timing --------------------------------------------------------
+    torch.cuda.synchronize()
+    barrier(world)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xff)
+                starts[i].record(stream)
+                rec.reconstruct_device(hits, offs, stream=stream)
+                ends[i].record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ms = max_over_ranks(ms, world)
+    value = world * args.steps / (ms / 1000.0)
+    clocks = clk.summary()
+
+    # ---- vote kernel alone (roofline), same stream, same call ----------------------------
+    vote_ms, stage_ms = vote_kernel_ms(rec, hits, offs, stream, flush, max(3, args.steps // 3))
+
+    # ---- end to end through the host C-ABI path ----------------------------------------
+    hp = torch.from_numpy(batch.packed()).pin_memory()
+    op = torch.from_numpy(batch.offsets.astype(np.int64)).pin_memory()
+    rec.reconstruct_host(hp, op, stream=stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rec.reconstruct_host(hp, op, stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    out = rec.out
+    h2d = batch.n_hits * 16 + (batch.n_events + 1) * 8
+    d2h = int(out.n_candidates) * 48 + int(out.n_hit_ids) * 4 + 8 * (batch.n_events + 1) + 4 * batch.n_events + 128
+
+    peaks = measured_peaks()
+    dev = torch.cuda.get_device_properties(local)
+    sm_count = dev.multi_processor_count
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    # FP32 lane-operation peak: 128 FP32 lanes per SM per clock
+    alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12
+    alg_ops = (PREFILTER_OPS * stats["n_triplets"]) / 1e12
+    achieved = alg_ops / (vote_ms / 1000.0) if vote_ms else None
+    line = {
+        "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "events_per_step": 1, "hits_per_event": batch.n_hits,
+                   "triplets_per_event": n_trip, "bins": rec.lib.trk_histogram_size(rec.h),
+                   "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas"},
+        "hit_triplets_per_s": value * n_trip,
+        "stats": {k: stats[k] for k in ("n_triplets", "n_fit", "n_votes", "n_fp64", "n_candidates",
+                                        "n_hit_ids", "n_work_items")},
+        "roofline": {"bound": "alu", "kernel": "k_vote", "achieved": achieved, "peak": alu_peak,
+                     "unit": "TFLOP/s", "frac": (achieved / alu_peak) if achieved else None,
+                     "traffic": None, "vote_kernel_ms": vote_ms,
+                     "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (median SM clock under load)"
+                                   % (sm_count, sm_mhz),
+                     "achieved_basis": "%d FP32 ops of the curvature test per enumerated triplet"
+                                       % PREFILTER_OPS},
+        "e2e": {"value": world * args.steps / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "stage_ms": stage_ms,
+        "clocks": clocks,
+        "gpu_launches": args.steps * LAUNCHES_PER_CALL,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        trip_s, cores, sample = cpu_baseline(cfg, batch, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": trip_s / n_trip, "unit": "events/s", "cores": cores,
+                                "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    rec.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# kernels of one trk_reconstruct call for a one-event batch: pack, schedule, vote,
+# 2 peak passes, 3 scan kernels x 3 scans, candidate emission, assignment, hit lists,
+# compaction, finalize
+LAUNCHES_PER_CALL = 1 + 1 + 1 + 2 + 9 + 1 + 1 + 1 + 1 + 1
+
+
+def vote_kernel_ms(rec, hits, offs, stream, flush, reps):
+    """Average device time of the vote kernel over `reps` calls, from the CUDA events the
+    library records around it on the call's stream (L2 flushed before each call)."""
+    import torch
+    tot = 0.0
+    stages = {}
+    for i in range(reps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xff)
+            rec.reconstruct_device(hits, offs, stream=stream)
+        st = rec.stage_ms(stream)
+        tot += st["vote"]
+        for k, v in st.items():
+            stages[k] = stages.get(k, 0.0) + v / reps
+    return tot / reps, stages
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * trk -- GB300-native displaced-track Hough transform (C ABI).
+ *
+ * The method (paper: "GPU Enhancement of the Trigger to Extend Physics Reach at the LHC",
+ * Sec. 7 and Fig. 3, Sec. 8): every combination of hits maps to a point of a binned
+ * track-parameter space, votes accumulate there, local maxima are track candidates and
+ * their hits are handed on (Sec. 8, the fit after candidate finding).  Here the
+ * combinations are hit triplets, one hit from each layer of a listed layer triple, and
+ * the parameter space is the 5-parameter helix (phi0, q/pT, d0, cot(theta), z0) about
+ * the coordinate origin with no beam-spot constraint, so that displaced tracks survive
+ * (Sec. 8: curved displaced tracks need a parameter space beyond the two-parameter
+ * interaction-point-constrained one; circles are fixed by centre and radius).
+ *
+ * Conventions (readings of the paper, which fixes none of them): units cm, GeV, T; field
+ * along +z; pT = K B R with K = 0.299792458e-2 GeV/(T cm); positive charges turn
+ * clockwise seen from +z, so q = -sign(D) with D = (p2 - p1) x (p3 - p1) in the
+ * transverse plane (hits in layer order a, b, c); perigee P = closest point of the
+ * circle to the origin, phi0 = direction of motion at P in [-pi, pi),
+ * d0 = -P_x sin(phi0) + P_y cos(phi0); s_k = 2R asin(|p_k - P| / 2R);
+ * (cot(theta), z0) = unweighted least-squares line z = z0 + s cot(theta) over the three
+ * hits; bin index floor((p - lo) / ((hi - lo)/n)), a triplet votes iff all five
+ * parameters are in range, periodic dimensions are wrapped first; bins are numbered
+ * row-major with phi0 slowest.  A bin is a candidate iff its count is >= threshold and
+ * it beats every one of its 3^5 - 1 neighbours: >= all of them, and > those with a
+ * smaller bin number.  A candidate's hits are the sorted union of the hits of the
+ * triplets that voted for it; its parameters are its bin centre.
+ *
+ * Everything on the device runs in the library's own sm_103a kernels.  All functions
+ * return 0 (TRK_OK) or a negative TRK_ERR_* code; none throws; none frees caller memory.
+ * A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef TRK_H
+#define TRK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TRK_MAX_LAYERS 64
+#define TRK_MAX_TRIPLES 512
+
+/* return codes */
+#define TRK_OK 0
+#define TRK_ERR_INVALID (-1)  /* bad argument: null pointer, bad size, bad geometry/binning */
+#define TRK_ERR_CAPACITY (-2) /* some event exceeded a capacity; see the per-event status */
+#define TRK_ERR_CUDA (-3)     /* a CUDA call failed; trk_last_error() has the text */
+#define TRK_ERR_NOMEM (-4)    /* device or pinned-host allocation failed */
+
+/* per-event status bits (an event with a non-zero status has no candidates: like a
+ * problematic event in the filter farm, it is passed on unprocessed) */
+#define TRK_EV_BAD_HIT 1        /* layer id out of range or non-finite coordinate */
+#define TRK_EV_TOO_MANY_HITS 2  /* more hits than trk_options.max_hits_per_event */
+#define TRK_EV_VOTE_OVERFLOW 4  /* the call's vote list overflowed */
+#define TRK_EV_CAND_OVERFLOW 8  /* the call's candidate or assignment capacity overflowed */
+#define TRK_EV_BAD_OFFSETS 16   /* event_offsets not non-decreasing within [0, n_hits] */
+
+/* One hit: 16 bytes, float32 position in cm and the layer index (0 .. n_layers-1). */
+typedef struct trk_hit {
+    float x, y, z;
+    int32_t layer;
+} trk_hit;
+
+/* Barrel geometry.  Only b_tesla, n_layers and the layer triples enter the arithmetic;
+ * radius/z_half describe the detector for bookkeeping. */
+typedef struct trk_geometry {
+    int32_t n_layers;                       /* 3 .. TRK_MAX_LAYERS */
+    int32_t n_triples;                      /* 1 .. TRK_MAX_TRIPLES */
+    double b_tesla;                         /* > 0 */
+    double radius[TRK_MAX_LAYERS];
+    double z_half[TRK_MAX_LAYERS];
+    int32_t triples[TRK_MAX_TRIPLES][3];    /* layer ids (a, b, c), pairwise distinct */
+} trk_geometry;
+
+/* Binning of (phi0, q/pT, d0, cot(theta), z0) in that order. */
+typedef struct trk_binning {
+    double lo[5], hi[5];                    /* lo < hi */
+    int32_t n[5];                           /* >= 1; product < 2^32; n[3]*n[4] <= 8192 */
+    int32_t periodic;                       /* bit k set: dimension k wraps (phi0: bit 0) */
+    int32_t threshold;                      /* minimum votes of a candidate, >= 1 */
+    float sagitta_fp64_cm;                  /* FP32 fits with |D| / |p3 - p1| at or below
+                                               this are recomputed in FP64 (0: only D == 0) */
+} trk_binning;
+
+/* Capacities and tuning; trk_options_default() fills sensible values.  All device memory
+ * is allocated once in trk_create. */
+typedef struct trk_options {
+    int32_t device;                         /* CUDA device ordinal */
+    int32_t max_events;                     /* events per call (histogram slots) */
+    int64_t max_hits;                       /* hits per call */
+    int32_t max_hits_per_event;             /* <= 1 << 20 */
+    int64_t vote_capacity;                  /* accepted triplets per call */
+    int64_t cand_capacity;                  /* candidates per call */
+    int64_t assign_capacity;                /* sum over candidates of 3 x votes per call */
+    int64_t peak_scratch_bytes;             /* scratch for the peak filter (>= 8 B x bins) */
+    int32_t tile_i, tile_j;                 /* pair tile of the vote kernel; tile_i*tile_j
+                                               in {64, 128, 256} */
+    int32_t k_chunk;                        /* outer-layer hits staged per shared chunk */
+    int32_t blocks_per_sm;                  /* persistent vote blocks per SM (0: auto) */
+    int32_t use_graph;                      /* capture each call shape in a CUDA graph */
+} trk_options;
+
+/* One candidate (48 bytes). */
+typedef struct trk_candidate {
+    uint32_t bin;                           /* row-major bin inside its event's histogram */
+    int32_t event;                          /* event index within the call */
+    int32_t votes;                          /* the bin's count */
+    int32_t n_hits;                         /* number of assigned hits */
+    int64_t hit_off;                        /* offset of its hits in hit_ids */
+    float params[5];                        /* bin centre (phi0, q/pT, d0, cot, z0) */
+    int32_t reserved;
+} trk_candidate;
+
+/* Results of one call.  Device arrays and host arrays are owned by the library and
+ * stay valid until the next trk_reconstruct* on the same handle or trk_destroy. */
+typedef struct trk_candidates {
+    int32_t n_events;
+    int64_t n_candidates;                   /* total over the call */
+    int64_t n_hit_ids;                      /* total over the call */
+    const int64_t *cand_off;                /* host [n_events + 1]: candidates of event e are
+                                               cand[cand_off[e] .. cand_off[e+1]) */
+    const int32_t *status;                  /* host [n_events]: TRK_EV_* bits */
+    const trk_candidate *d_cand;            /* device [n_candidates], sorted by (event, bin) */
+    const int32_t *d_hit_ids;               /* device [n_hit_ids]: input hit indices (global,
+                                               i.e. into the call's hit array), sorted per
+                                               candidate */
+    const trk_candidate *h_cand;            /* host copies, filled only by
+                                               trk_reconstruct_host (else NULL) */
+    const int32_t *h_hit_ids;
+} trk_candidates;
+
+/* Counters of the last call. */
+typedef struct trk_stats {
+    int64_t n_triplets;                     /* sum over events and triples of |La||Lb||Lc| */
+    int64_t n_fit;                          /* triplets through the full FP32 fit */
+    int64_t n_votes;                        /* accepted triplets */
+    int64_t n_fp64;                         /* fits redone in FP64 */
+    int64_t n_candidates;
+    int64_t n_hit_ids;
+    int64_t n_work_items;
+    double ms_total;                        /* device time of the call (events on the stream) */
+} trk_stats;
+
+typedef struct trk_ctx trk_ctx;
+
+/* Defaults for a workload of at most max_events events and max_hits hits per call. */
+void trk_options_default(trk_options *opt, int32_t max_events, int64_t max_hits);
+
+/* Create a handle: validates geometry and binning, copies them to the device and
+ * allocates every pool.  *out receives the handle (NULL on failure). */
+int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk_binning *binning,
+               const trk_options *options /* nullable: defaults for 1 event */);
+
+/* Reconstruct n_events events.  hits: DEVICE pointer to n_hits trk_hit; event_offsets:
+ * DEVICE pointer to n_events + 1 int64, event e owning hits [off[e], off[e+1]).  Runs on
+ * `stream` (a cudaStream_t, NULL = the legacy default stream) and returns after the
+ * per-event counts reached the host (the call's only synchronisation).  Returns TRK_OK,
+ * TRK_ERR_CAPACITY (some event flagged, the others are complete), or an error. */
+int trk_reconstruct(trk_ctx *h, const trk_hit *hits, int64_t n_hits,
+                    const int64_t *event_offsets, int32_t n_events, trk_candidates *out,
+                    void *stream);
+
+/* Same, from HOST buffers (any host memory): copies the hits in, reconstructs and copies
+ * the candidates and hit ids back to library-owned pinned host memory (out->h_cand,
+ * out->h_hit_ids).  The end-to-end path of a caller whose events live in host memory. */
+int trk_reconstruct_host(trk_ctx *h, const trk_hit *hits, int64_t n_hits,
+                         const int64_t *event_offsets, int32_t n_events,
+                         trk_candidates *out, void *stream);
+
+/* Destroy a handle and free everything it owns.  NULL is accepted. */
+int trk_destroy(trk_ctx *h);
+
+/* Counters of the last call. */
+int trk_get_stats(trk_ctx *h, trk_stats *out);
+
+/* Copy event e's dense vote histogram of the last call (n bins int32, row-major) to the
+ * DEVICE buffer dst, on `stream`. */
+int trk_get_histogram(trk_ctx *h, int32_t event, int32_t *dst, void *stream);
+
+/* Number of bins of one event's histogram. */
+int64_t trk_histogram_size(const trk_ctx *h);
+
+/* The last call's accepted triplets, decoded: for vote v, dst[4v..4v+3] = (event, i, j, k)
+ * with i, j, k input hit indices (global) from layers a, b, c, and bins[v] its bin.  DEVICE
+ * buffers of capacity `cap` votes; *n_out receives the number of votes (all are written
+ * only if n_out <= cap).  Synchronises the stream. */
+int trk_get_votes(trk_ctx *h, int32_t *dst, uint32_t *bins, int64_t cap, int64_t *n_out,
+                  void *stream);
+
+/* Fit explicit triplets with exactly the arithmetic of the vote kernel: for t < n,
+ * ijk[3t..3t+2] are indices into hits[0 .. n_hits) (DEVICE).  Writes params[5t..5t+4]
+ * (FP32, NaN when degenerate), bins[t] (valid when accepted) and flags[t]: bit 0
+ * accepted, bit 1 computed in FP64, bit 2 degenerate, bit 3 index out of range (nothing
+ * else written for that triplet).  All DEVICE buffers.  Asynchronous. */
+int trk_fit_triplets(trk_ctx *h, const trk_hit *hits, int64_t n_hits, const int32_t *ijk,
+                     int64_t n, float *params, uint32_t *bins, int32_t *flags, void *stream);
+
+/* Device time (ms) of the stages of the last call, from CUDA events the library records on
+ * the call's stream: ms[0] the vote kernel (triplet fit + vote), ms[1] argument copy,
+ * histogram clear, packing and scheduling, ms[2] the peak finder, ms[3] candidate emission,
+ * ms[4] hit assignment, compaction and the result copies; ms[5..7] = 0.  Synchronises. */
+int trk_profile_stages(trk_ctx *h, float ms[8], void *stream);
+
+/* Text of the last error on this handle (or of the last failed trk_create if h NULL). */
+const char *trk_last_error(const trk_ctx *h);
+
+/* Library version string. */
+const char *trk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRK_H */

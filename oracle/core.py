@@ -120,6 +120,7 @@ def enumerate_batch(xyz, layer, offsets, setup: OracleSetup, n_threads: int = 0)
             ijk=arr(res.acc_ijk, np.int32, 3 * na).reshape(-1, 3),
             bin=arr(res.acc_bin, np.uint64, na).astype(np.int64),
             amb=arr(res.acc_amb, np.uint8, na).astype(bool),
+            amb_bits=arr(res.acc_amb, np.uint8, na),
             par=arr(res.acc_par, np.float64, 5 * na).reshape(-1, 5),
             near_event=arr(res.near_event, np.int32, nn),
             near_ijk=arr(res.near_ijk, np.int32, 3 * nn).reshape(-1, 3),
@@ -146,7 +147,8 @@ def fit_list(xyz, layer, ijk, setup: OracleSetup, n_threads: int = 0) -> dict:
     lib.orc_fit_list(hits.ctypes.data, ijk.ctypes.data, C.c_int64(n), C.byref(s),
                      C.c_int32(n_threads), par.ctypes.data, binv.ctypes.data,
                      status.ctypes.data, amb.ctypes.data)
-    return dict(par=par, bin=binv.astype(np.int64), status=status, amb=amb.astype(bool))
+    return dict(par=par, bin=binv.astype(np.int64), status=status, amb=amb.astype(bool),
+                amb_bits=amb)
 
 
 def fit_one(p1, p2, p3, b_tesla: float):

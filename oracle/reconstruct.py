@@ -37,35 +37,45 @@ def histogram(event: np.ndarray, bins: np.ndarray, n_events: int):
     return out
 
 
-def peaks(ubins: np.ndarray, counts: np.ndarray, setup: OracleSetup):
+def peaks(ubins: np.ndarray, counts: np.ndarray, setup: OracleSetup, chunk: int = 65536,
+          only_phi0=None):
     """Candidates of one event's histogram given as sorted non-empty bins and counts.
-    Returns (candidate bins ascending, their votes)."""
+    Returns (candidate bins ascending, their votes).  Bins above threshold are examined
+    in chunks only to bound memory; each bin's test is independent of the others, so
+    `only_phi0` (a set of phi0 bin indices) restricts the answer to those slabs without
+    changing it there."""
     T = setup.threshold
     sel = counts >= T
-    over, hv = ubins[sel], counts[sel]
-    if len(over) == 0:
+    if only_phi0 is not None:
+        stride0 = int(np.prod(setup.n[1:]))
+        sel &= np.isin(ubins // stride0, np.asarray(sorted(only_phi0), dtype=np.int64))
+    over_all, hv_all = ubins[sel], counts[sel]
+    if len(over_all) == 0:
         return np.zeros(0, np.int64), np.zeros(0, np.int64)
     dims = tuple(int(x) for x in setup.n)
-    idx = np.stack(np.unravel_index(over, dims), axis=1)          # (m, 5)
     offs = neighbour_offsets()                                      # (242, 5)
-    nidx = idx[:, None, :] + offs[None, :, :]                       # (m, 242, 5)
-    valid = np.ones(nidx.shape[:2], dtype=bool)
-    for k in range(5):
-        if setup.periodic[k]:
-            nidx[:, :, k] %= dims[k]
-        else:
-            valid &= (nidx[:, :, k] >= 0) & (nidx[:, :, k] < dims[k])
-    nidx = np.where(valid[:, :, None], nidx, 0)
-    nbin = np.ravel_multi_index(tuple(nidx[:, :, k] for k in range(5)), dims)
-    valid &= nbin != over[:, None]
-    pos = np.searchsorted(ubins, nbin)
-    pos_c = np.minimum(pos, len(ubins) - 1)
-    present = ubins[pos_c] == nbin
-    ncnt = np.where(present, counts[pos_c], 0)
-    ge = np.all(~valid | (hv[:, None] >= ncnt), axis=1)
-    gt_lower = np.all(~valid | (nbin > over[:, None]) | (hv[:, None] > ncnt), axis=1)
-    keep = ge & gt_lower
-    return over[keep], hv[keep]
+    keep_all = np.zeros(len(over_all), dtype=bool)
+    for c0 in range(0, len(over_all), chunk):
+        over, hv = over_all[c0:c0 + chunk], hv_all[c0:c0 + chunk]
+        idx = np.stack(np.unravel_index(over, dims), axis=1)          # (m, 5)
+        nidx = idx[:, None, :] + offs[None, :, :]                       # (m, 242, 5)
+        valid = np.ones(nidx.shape[:2], dtype=bool)
+        for k in range(5):
+            if setup.periodic[k]:
+                nidx[:, :, k] %= dims[k]
+            else:
+                valid &= (nidx[:, :, k] >= 0) & (nidx[:, :, k] < dims[k])
+        nidx = np.where(valid[:, :, None], nidx, 0)
+        nbin = np.ravel_multi_index(tuple(nidx[:, :, k] for k in range(5)), dims)
+        valid &= nbin != over[:, None]
+        pos = np.searchsorted(ubins, nbin)
+        pos_c = np.minimum(pos, len(ubins) - 1)
+        present = ubins[pos_c] == nbin
+        ncnt = np.where(present, counts[pos_c], 0)
+        ge = np.all(~valid | (hv[:, None] >= ncnt), axis=1)
+        gt_lower = np.all(~valid | (nbin > over[:, None]) | (hv[:, None] > ncnt), axis=1)
+        keep_all[c0:c0 + chunk] = ge & gt_lower
+    return over_all[keep_all], hv_all[keep_all]
 
 
 def bin_centres(cand_bins: np.ndarray, setup: OracleSetup) -> np.ndarray:

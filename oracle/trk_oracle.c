@@ -13,8 +13,10 @@
  *        unweighted least-squares line z = z0 + s cot(theta) over the three (s_k, z_k);
  *     2. the five bin indices; the triplet is accepted iff all five parameters lie in
  *        range, and then votes once into bin (phi0, q/pT, d0, cot, z0), row-major;
- *     3. an edge-ambiguity flag: some parameter lies within eps of a bin edge or range
- *        limit, eps = eps_rel * max(|p|, half-range).
+ *     3. ambiguity flags: some parameter lies within eps of a bin edge or range limit,
+ *        eps = eps_rel * max(|p|, half-range) (bit 0), the triplet is rejected only by
+ *        parameters within eps outside their ranges (bit 1), or a hit lies within
+ *        eps_rel * pi of the point of the circle opposite the perigee (bit 2).
  *
  * Paper: Sec. 7 and Fig. 3 (each hit set maps to many parameter points, votes are
  * accumulated, peaks are tracks); Sec. 8 (curved features need more parameters,
@@ -30,7 +32,12 @@
  *     (|c|^2 - R^2)/(|c| + R) with |c|^2 - R^2 = |p1|^2 + 2 p1.(c - p1) (an identity,
  *     used because the direct difference of two large numbers loses all digits);
  *   - D == 0: straight line through p1 and p3, q/pT = 0, P the foot of the normal;
- *   - s_k = 2R asin(|p_k - P| / (2R)) (|p_k - P| on a straight line);
+ *   - s_k = +-2R asin(|p_k - P| / (2R)) (+-|p_k - P| on a straight line): the path length
+ *     from the perigee, positive for a hit after P in the direction of motion and negative
+ *     for one before it (the sign of (p_k - P) . (cos phi0, sin phi0), + when it is 0),
+ *     so that z = z0 + s cot(theta) holds on both branches of the helix through P;
+ *     a hit within eps of the point opposite P (where that sign is undefined) makes the
+ *     triplet ambiguous;
  *   - bins: idx = floor((p - lo) / ((hi - lo)/n)), accepted iff lo <= p < hi; a periodic
  *     dimension is wrapped into [lo, hi) first.
  * Degenerate triplets (circle centred on the origin, or three equal arc lengths) have
@@ -45,6 +52,7 @@
 #endif
 
 #define ORC_K 0.299792458e-2
+#define ORC_PI 3.14159265358979323846
 
 typedef struct {
     float x, y, z;
@@ -67,9 +75,10 @@ typedef struct {
     int32_t *acc_event;     /* [n_acc] */
     int32_t *acc_ijk;       /* [n_acc * 3] input hit indices (global) */
     uint64_t *acc_bin;      /* [n_acc] row-major bin inside the event's histogram */
-    uint8_t *acc_amb;       /* [n_acc] edge-ambiguous */
+    uint8_t *acc_amb;       /* [n_acc] ambiguity bits (1 edge, 4 antipode) */
     double *acc_par;        /* [n_acc * 5] */
-    int64_t n_near;         /* rejected, but every out-of-range parameter within eps */
+    int64_t n_near;         /* rejected, but every out-of-range parameter within eps, or
+                               antipode-ambiguous */
     int32_t *near_event;
     int32_t *near_ijk;
     int64_t n_triplets;     /* sum over events and triples of |La||Lb||Lc| */
@@ -80,9 +89,10 @@ enum { ORC_OK = 0, ORC_DEGENERATE = 1 };
 
 /* Helix of the triplet.  Returns ORC_OK and par = (phi0, q/pT, d0, cot, z0), or
  * ORC_DEGENERATE. */
-int orc_fit(const double *p1, const double *p2, const double *p3, double b_tesla,
-            double *par)
+int orc_fit_flags(const double *p1, const double *p2, const double *p3, double b_tesla,
+                  double eps_rel, double *par, int *antipode)
 {
+    *antipode = 0;
     const double ux = p2[0] - p1[0], uy = p2[1] - p1[1];
     const double vx = p3[0] - p1[0], vy = p3[1] - p1[1];
     const double D = ux * vy - uy * vx;
@@ -121,17 +131,22 @@ int orc_fit(const double *p1, const double *p2, const double *p3, double b_tesla
         R = INFINITY;
     }
     const double *pk[3] = {p1, p2, p3};
+    const double tx = cos(phi0), ty = sin(phi0);
     double s[3];
     for (int k = 0; k < 3; ++k) {
         const double dx = pk[k][0] - px, dy = pk[k][1] - py;
         const double chord = sqrt(dx * dx + dy * dy);
+        const double sign = (dx * tx + dy * ty) >= 0.0 ? 1.0 : -1.0;
         if (straight) {
-            s[k] = chord;
+            s[k] = sign * chord;
         } else {
             double a = chord / (2.0 * R);
             if (a > 1.0)
                 a = 1.0;
-            s[k] = 2.0 * R * asin(a);
+            const double half_angle = asin(a);
+            if (2.0 * half_angle >= ORC_PI * (1.0 - eps_rel))
+                *antipode = 1;
+            s[k] = sign * 2.0 * R * half_angle;
         }
     }
     const double sbar = (s[0] + s[1] + s[2]) / 3.0;
@@ -151,6 +166,13 @@ int orc_fit(const double *p1, const double *p2, const double *p3, double b_tesla
     par[3] = cot;
     par[4] = z0;
     return ORC_OK;
+}
+
+/* Helix of the triplet (see orc_fit_flags), without the antipode flag. */
+int orc_fit(const double *p1, const double *p2, const double *p3, double b_tesla, double *par)
+{
+    int anti;
+    return orc_fit_flags(p1, p2, p3, b_tesla, 1e-5, par, &anti);
 }
 
 /* Bin the parameters.  Returns 1 if accepted (all in range) with *bin set; sets *amb if
@@ -326,15 +348,16 @@ int orc_run(const orc_hit *hits, int64_t n_hits, const int64_t *offsets, int32_t
                 const int32_t hk = lay_idx[kk];
                 const double p3[3] = {hits[hk].x, hits[hk].y, hits[hk].z};
                 double par[5];
-                if (orc_fit(p1, p2, p3, s->b_tesla, par) != ORC_OK) {
+                int anti;
+                if (orc_fit_flags(p1, p2, p3, s->b_tesla, s->eps_rel, par, &anti) != ORC_OK) {
                     buf->n_degenerate++;
                     continue;
                 }
                 uint64_t bin;
                 int amb, near;
                 if (orc_bin(s, par, &bin, &amb, &near))
-                    ub_push_acc(buf, hi_, hj, hk, bin, amb, par);
-                else if (near)
+                    ub_push_acc(buf, hi_, hj, hk, bin, amb | (anti ? 4 : 0), par);
+                else if (near || anti)
                     ub_push_near(buf, hi_, hj, hk);
             }
         }
@@ -401,7 +424,8 @@ void orc_result_free(orc_result *res)
 
 /* Fit and bin an explicit list of triplets (input hit indices), for sampled checks at
  * sizes the full enumeration cannot reach.  status[t]: 0 accepted, 1 rejected,
- * 2 degenerate; amb[t] edge-ambiguous or near; par/bin filled when not degenerate. */
+ * 2 degenerate; amb[t] ambiguity bits (1 edge, 2 near a range limit, 4 antipode);
+ * par/bin filled when not degenerate. */
 void orc_fit_list(const orc_hit *hits, const int32_t *ijk, int64_t n, const orc_setup *s,
                   int32_t n_threads, double *par, uint64_t *bin, int32_t *status,
                   uint8_t *amb)
@@ -415,7 +439,8 @@ void orc_fit_list(const orc_hit *hits, const int32_t *ijk, int64_t n, const orc_
         const orc_hit *a = hits + ijk[3 * t], *b = hits + ijk[3 * t + 1], *c = hits + ijk[3 * t + 2];
         const double p1[3] = {a->x, a->y, a->z}, p2[3] = {b->x, b->y, b->z},
                      p3[3] = {c->x, c->y, c->z};
-        if (orc_fit(p1, p2, p3, s->b_tesla, par + 5 * t) != ORC_OK) {
+        int anti;
+        if (orc_fit_flags(p1, p2, p3, s->b_tesla, s->eps_rel, par + 5 * t, &anti) != ORC_OK) {
             status[t] = 2;
             amb[t] = 0;
             bin[t] = 0;
@@ -424,7 +449,7 @@ void orc_fit_list(const orc_hit *hits, const int32_t *ijk, int64_t n, const orc_
         int am, near;
         const int acc = orc_bin(s, par + 5 * t, bin + t, &am, &near);
         status[t] = acc ? 0 : 1;
-        amb[t] = (uint8_t)(am || near);
+        amb[t] = (uint8_t)((am ? 1 : 0) | (near ? 2 : 0) | (anti ? 4 : 0));
     }
 }
 

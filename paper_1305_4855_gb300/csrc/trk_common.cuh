@@ -1,0 +1,438 @@
+// Internal device-side definitions shared by the kernels of libtrk (not part of the ABI).
+//
+// The helix-from-triplet arithmetic below follows the readings stated in include/trk.h
+// (paper Sec. 8: a circle is fixed by centre and radius; a curved displaced track needs a
+// parameter space beyond the interaction-point-constrained one).  It is written for FP32
+// on the CUDA cores in forms that avoid cancellation, with an FP64 recomputation for the
+// near-collinear fits (|D| / |p3 - p1| at or below a threshold, D == 0 included) and for
+// any degenerate intermediate.  The library is compiled with -fmad=false: every fused
+// multiply-add below is explicit, so the staged evaluation inside the vote kernel and the
+// one-shot evaluation of trk_fit_triplets round identically.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "trk.h"
+
+namespace trk {
+
+constexpr double kGeVPerTeslaCm = 0.299792458e-2;
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Constants of the fit and of the binning, passed by value to the kernels.
+struct FitConst {
+    float kB;            // K * B [GeV / cm]
+    float pre_k2;        // curvature prefilter: 4 D^2 <= pre_k2 * |u|^2 |v|^2 |w|^2
+    float sag2;          // FP64 recomputation when D^2 <= sag2 * |v|^2
+    int periodic;        // bit 0 only (phi0)
+    float lo[5], hi[5], inv_w[5];
+    float period0;       // hi[0] - lo[0] when periodic
+    int n[5];
+    uint32_t stride[5];  // row-major strides, stride[4] = 1
+    uint32_t nbins;
+    double kB_d;
+    double lo_d[5], hi_d[5], w_d[5];
+};
+
+// Geometry needed on the device.
+struct DevGeo {
+    int n_layers;
+    int n_triples;
+    int triples[TRK_MAX_TRIPLES][3];
+};
+
+// Per-call arguments, copied to the device before the launches so that a captured
+// graph can be replayed for new inputs.
+struct CallArgs {
+    const trk_hit *hits;
+    const int64_t *offsets;
+    int64_t n_hits;
+    int32_t n_events;
+    int32_t pad;
+};
+
+// Device counters of one call (zeroed at its start).
+struct Counters {
+    unsigned long long work_next;    // persistent vote kernel work counter
+    unsigned long long n_votes;      // votes appended (may exceed capacity)
+    unsigned long long n_chunks;     // vote chunks appended
+    unsigned long long n_fit;        // triplets through the full FP32 fit
+    unsigned long long n_fp64;       // triplets recomputed in FP64
+    unsigned long long n_items;      // work items of the call
+    unsigned long long n_triplets;   // sum |La||Lb||Lc|
+    unsigned long long n_cand;       // candidates (may exceed capacity)
+    unsigned long long n_assign;     // 3 x votes over candidates
+    unsigned long long n_hit_ids;    // assigned hit ids
+    unsigned long long overflow;     // bit 0 candidate capacity, bit 1 assignment capacity
+    unsigned long long pad[5];
+};
+
+// A run of consecutive votes of one work item in the vote list.
+struct VoteChunk {
+    int32_t item;
+    int32_t count;
+    int64_t offset;
+};
+
+// vote record: low 32 bits the bin, high 32 bits (pair in tile << 24) | k in layer c
+__host__ __device__ inline uint64_t make_vote(uint32_t bin, uint32_t pair, uint32_t k)
+{
+    return (uint64_t)bin | ((uint64_t)((pair << 24) | (k & 0xffffffu)) << 32);
+}
+
+// Arguments of the vote kernel.
+struct VoteArgs {
+    const float4 *packed;        // layer-sorted hits: x, y, z, input index (int bits)
+    const int32_t *lay_off;      // [event][n_layers + 1] positions in `packed`
+    const int64_t *item_off;     // [n_events * n_triples + 1] work-item prefix
+    const DevGeo *geo;
+    const CallArgs *args;
+    int32_t *status;             // per-event status (vote overflow is or-ed in)
+    int32_t *hist;               // [event][nbins]
+    uint64_t *votes;             // [chunk_cap * 32]
+    int32_t *chunk_item;         // [chunk_cap] item of each 32-slot chunk (-1: empty)
+    int32_t *chunk_count;        // [chunk_cap]
+    int64_t chunk_cap;
+    Counters *ctr;
+    FitConst C;
+};
+
+// Arguments of the assignment kernels.
+struct AssignArgs {
+    const uint64_t *votes;
+    const int32_t *chunk_item;
+    const int32_t *chunk_count;
+    int64_t chunk_cap;
+    const int64_t *item_off;
+    const DevGeo *geo;
+    const int32_t *lay_off;
+    const CallArgs *args;
+    const float4 *packed;
+    const int64_t *ev_begin;
+    const uint32_t *cbits;
+    const uint32_t *wprefix;
+    int64_t W;
+    const int64_t *vote_off;
+    int32_t *fill;
+    int32_t *assign;
+    int64_t assign_cap;
+    int64_t cand_cap;
+    Counters *ctr;
+    int ti, tj;
+};
+
+// ---------------------------------------------------------------------------------------
+// FP32 helix fit
+// ---------------------------------------------------------------------------------------
+
+// a*d - b*c with one rounding error of the products compensated (Kahan's FMA
+// determinant; Jeannerod, Louvet, Muller, Math. Comp. 82 (2013): error <= 2 ulp).
+__device__ __forceinline__ float det2(float a, float b, float c, float d)
+{
+    const float w = b * c;
+    const float e = fmaf(-b, c, w);
+    const float f = fmaf(a, d, -w);
+    return f + e;
+}
+
+// Result of the transverse + longitudinal part of the fit, everything but phi0.
+struct FitB {
+    float cx, cy;        // circle centre
+    float sgn;           // sign(D): +1 counter-clockwise
+    float qopt, d0, cot, z0;
+};
+
+enum FitStatus { kReject = 0, kPass = 1, kNeedFp64 = 2 };
+
+// Wraps the periodic dimension 0 into [lo, hi); returns false when p is out of range.
+__device__ __forceinline__ bool bin_f32(const FitConst &C, int k, float p, uint32_t &idx)
+{
+    if (k == 0 && (C.periodic & 1)) {
+        if (p >= C.hi[0])
+            p -= C.period0;
+        else if (p < C.lo[0])
+            p += C.period0;
+    }
+    if (!(p >= C.lo[k] && p < C.hi[k]))
+        return false;
+    int i = (int)floorf((p - C.lo[k]) * C.inv_w[k]);
+    i = i < 0 ? 0 : (i >= C.n[k] ? C.n[k] - 1 : i);
+    idx = (uint32_t)i;
+    return true;
+}
+
+__device__ __forceinline__ bool in_range_f32(const FitConst &C, int k, float p)
+{
+    return p >= C.lo[k] && p < C.hi[k];
+}
+
+// Everything but phi0 for points p1, p2, p3 (x, y, z in .x .y .z).
+__device__ __forceinline__ int fit_stage_b(const float4 &p1, const float4 &p2, const float4 &p3,
+                                           const FitConst &C, FitB &r)
+{
+    const float ux = p2.x - p1.x, uy = p2.y - p1.y;
+    const float vx = p3.x - p1.x, vy = p3.y - p1.y;
+    const float wx = p3.x - p2.x, wy = p3.y - p2.y;
+    const float D = det2(ux, uy, vx, vy);
+    const float uu = fmaf(ux, ux, uy * uy);
+    const float vv = fmaf(vx, vx, vy * vy);
+    const float ww = fmaf(wx, wx, wy * wy);
+    if (D * D <= C.sag2 * vv)
+        return kNeedFp64;
+    // q/pT = -sign(D) / (K B R), R = |u||v||w| / (2|D|)
+    const float sq = sqrtf(uu * vv * ww);
+    const float qopt = (-2.0f * D) / (C.kB * sq);
+    if (!in_range_f32(C, 1, qopt))
+        return kReject;
+    // centre c = p1 + (v_y|u|^2 - u_y|v|^2, u_x|v|^2 - v_x|u|^2) / (2D)
+    const float inv2d = 0.5f / D;
+    const float cpx = det2(vy, uy, vv, uu) * inv2d;
+    const float cpy = det2(ux, vx, uu, vv) * inv2d;
+    const float cx = p1.x + cpx, cy = p1.y + cpy;
+    const float R = sq * fabsf(inv2d);
+    const float cn = sqrtf(fmaf(cx, cx, cy * cy));
+    // |c| - R = (|c|^2 - R^2) / (|c| + R), |c|^2 - R^2 = |p1|^2 + 2 p1.(c - p1)
+    const float power = fmaf(p1.x, p1.x, p1.y * p1.y) + 2.0f * fmaf(p1.x, cpx, p1.y * cpy);
+    const float dist = power / (cn + R);
+    const float sgn = D > 0.0f ? 1.0f : -1.0f;
+    const float d0 = sgn * dist;
+    if (!in_range_f32(C, 2, d0))
+        return kReject;
+    if (!(cn > 0.0f) || !(R < 3.0e37f))
+        return kNeedFp64;
+    // perigee P = c (|c| - R) / |c|
+    const float f = dist / cn;
+    const float px = cx * f, py = cy * f;
+    const float inv2r = 0.5f / R;
+    const float twor = 2.0f * R;
+    // Signed path length s_k from P (negative for a hit before P in the direction of
+    // motion).  |s| = 2R asin(chord / 2R) while the chord is short, the sign from the
+    // projection on the direction of motion sgn (c_y, -c_x) / |c|; towards half a turn
+    // (chord -> 2R) the asin form is ill-conditioned in FP32, so there s is R times the
+    // signed central angle between P - c = -R c/|c| and p_k - c, from atan2.
+    const float ax = -R * (cx / cn), ay = -R * (cy / cn);
+    const float bx[3] = {-cpx, ux - cpx, vx - cpx};
+    const float by[3] = {-cpy, uy - cpy, vy - cpy};
+    float s[3];
+    const float4 *pk[3] = {&p1, &p2, &p3};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float dx = pk[k]->x - px, dy = pk[k]->y - py;
+        const float chord = sqrtf(fmaf(dx, dx, dy * dy));
+        const float x = chord * inv2r;
+        if (x <= 0.7f) {
+            const float m = twor * asinf(x);
+            s[k] = (sgn * det2(dx, dy, cx, cy) >= 0.0f) ? m : -m;
+        } else {
+            const float cr = det2(ax, ay, bx[k], by[k]);
+            const float dt = fmaf(ax, bx[k], ay * by[k]);
+            s[k] = sgn * R * atan2f(cr, dt);
+        }
+    }
+    // The slope needs only differences s_k - s_1; each absolute s_k carries its own
+    // rounding, which a hit with a large z residual and little lever turns into a large
+    // slope error.  The arc a between p1 and p_k from the chord |p_k - p1| (a difference
+    // of inputs) is accurate, and s_k - s_1 is one of a, -a, a - 2 pi R, 2 pi R - a: the
+    // one closest to the difference of the absolute values.
+    float dlt[3];
+    dlt[0] = 0.0f;
+    const float cu = sqrtf(uu), cv = sqrtf(vv);
+    const float turn = 6.2831853f * R;
+#pragma unroll
+    for (int k = 1; k < 3; ++k) {
+        const float ch = k == 1 ? cu : cv;
+        const float x = ch * inv2r;
+        float a;
+        if (x <= 0.7f) {
+            a = twor * asinf(x);
+        } else {
+            const float cr = det2(bx[0], by[0], bx[k], by[k]);
+            const float dt = fmaf(bx[0], bx[k], by[0] * by[k]);
+            a = R * fabsf(atan2f(cr, dt));
+        }
+        const float coarse = s[k] - s[0];
+        const float cand[4] = {a, -a, a - turn, turn - a};
+        float best = cand[0], berr = fabsf(cand[0] - coarse);
+#pragma unroll
+        for (int q = 1; q < 4; ++q) {
+            const float e = fabsf(cand[q] - coarse);
+            if (e < berr) {
+                berr = e;
+                best = cand[q];
+            }
+        }
+        dlt[k] = best;
+    }
+    const float dbar = (dlt[1] + dlt[2]) * (1.0f / 3.0f);
+    const float sbar = s[0] + dbar;
+    const float zbar = (p1.z + p2.z + p3.z) * (1.0f / 3.0f);
+    const float a0 = -dbar, a1 = dlt[1] - dbar, a2 = dlt[2] - dbar;
+    const float sss = fmaf(a0, a0, fmaf(a1, a1, a2 * a2));
+    const float ssz = fmaf(a0, p1.z - zbar, fmaf(a1, p2.z - zbar, a2 * (p3.z - zbar)));
+    if (!(sss > 0.0f))
+        return kNeedFp64;
+    const float cot = ssz / sss;
+    const float z0 = fmaf(-cot, sbar, zbar);
+    if (!in_range_f32(C, 3, cot) || !in_range_f32(C, 4, z0))
+        return kReject;
+    r.cx = cx;
+    r.cy = cy;
+    r.sgn = sgn;
+    r.qopt = qopt;
+    r.d0 = d0;
+    r.cot = cot;
+    r.z0 = z0;
+    return kPass;
+}
+
+// phi0 (direction of motion at the perigee: sgn (c_y, -c_x) / |c|) and the bin.
+// Returns false if some parameter falls out of range (only possible for phi0 when the
+// phi0 range is not periodic).
+__device__ __forceinline__ bool fit_stage_c(const FitB &r, const FitConst &C, float &phi0,
+                                            uint32_t &bin)
+{
+    phi0 = atan2f(-r.sgn * r.cx, r.sgn * r.cy);
+    uint32_t i0, i1, i2, i3, i4;
+    if (!bin_f32(C, 0, phi0, i0) || !bin_f32(C, 1, r.qopt, i1) || !bin_f32(C, 2, r.d0, i2) ||
+        !bin_f32(C, 3, r.cot, i3) || !bin_f32(C, 4, r.z0, i4))
+        return false;
+    bin = i0 * C.stride[0] + i1 * C.stride[1] + i2 * C.stride[2] + i3 * C.stride[3] + i4;
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// FP64 recomputation (near-collinear and degenerate FP32 fits)
+// ---------------------------------------------------------------------------------------
+
+enum { kFit64Accepted = 1, kFit64Degenerate = 2 };
+
+__device__ __forceinline__ bool bin_f64(const FitConst &C, int k, double p, uint32_t &idx)
+{
+    if (k == 0 && (C.periodic & 1)) {
+        const double period = C.hi_d[0] - C.lo_d[0];
+        if (p >= C.hi_d[0])
+            p -= period;
+        else if (p < C.lo_d[0])
+            p += period;
+    }
+    if (!(p >= C.lo_d[k] && p < C.hi_d[k]))
+        return false;
+    long long i = (long long)floor((p - C.lo_d[k]) / C.w_d[k]);
+    i = i < 0 ? 0 : (i >= C.n[k] ? C.n[k] - 1 : i);
+    idx = (uint32_t)i;
+    return true;
+}
+
+// Full fit in FP64.  Returns kFit64Accepted with par and bin, 0 when out of range,
+// kFit64Degenerate when the helix is undefined.
+static __device__ __noinline__ int fit_f64(const float4 &q1, const float4 &q2, const float4 &q3,
+                                    const FitConst &C, double par[5], uint32_t &bin)
+{
+    const double x1 = q1.x, y1 = q1.y, z1 = q1.z;
+    const double x2 = q2.x, y2 = q2.y, z2 = q2.z;
+    const double x3 = q3.x, y3 = q3.y, z3 = q3.z;
+    const double ux = x2 - x1, uy = y2 - y1, vx = x3 - x1, vy = y3 - y1;
+    const double D = __dsub_rn(__dmul_rn(ux, vy), __dmul_rn(uy, vx));
+    double phi0, qopt, d0, px, py, R;
+    const bool straight = (D == 0.0);
+    if (!straight) {
+        const double uu = __dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy));
+        const double vv = __dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy));
+        const double cpx = __dsub_rn(__dmul_rn(vy, uu), __dmul_rn(uy, vv)) / (2.0 * D);
+        const double cpy = __dsub_rn(__dmul_rn(ux, vv), __dmul_rn(vx, uu)) / (2.0 * D);
+        const double cx = x1 + cpx, cy = y1 + cpy;
+        const double sgn = D > 0.0 ? 1.0 : -1.0;
+        R = sqrt(__dadd_rn(__dmul_rn(cpx, cpx), __dmul_rn(cpy, cpy)));
+        qopt = -sgn / (C.kB_d * R);
+        const double cn = sqrt(__dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy)));
+        if (cn == 0.0)
+            return kFit64Degenerate;
+        const double power = __dadd_rn(__dadd_rn(__dmul_rn(x1, x1), __dmul_rn(y1, y1)),
+                                       2.0 * __dadd_rn(__dmul_rn(x1, cpx), __dmul_rn(y1, cpy)));
+        const double cmr = power / (cn + R);
+        px = cx * (cmr / cn);
+        py = cy * (cmr / cn);
+        phi0 = atan2(-sgn * cx, sgn * cy);
+        d0 = __dadd_rn(__dmul_rn(-px, sin(phi0)), __dmul_rn(py, cos(phi0)));
+    } else {
+        const double vn = sqrt(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)));
+        if (vn == 0.0)
+            return kFit64Degenerate;
+        const double tx = vx / vn, ty = vy / vn;
+        const double along = __dadd_rn(__dmul_rn(x1, tx), __dmul_rn(y1, ty));
+        px = x1 - along * tx;
+        py = y1 - along * ty;
+        phi0 = atan2(vy, vx);
+        d0 = __dadd_rn(__dmul_rn(-px, sin(phi0)), __dmul_rn(py, cos(phi0)));
+        qopt = 0.0;
+        R = 0.0;
+    }
+    const double xs[3] = {x1, x2, x3}, ys[3] = {y1, y2, y3}, zs[3] = {z1, z2, z3};
+    const double tx = cos(phi0), ty = sin(phi0);
+    double s[3];
+    for (int k = 0; k < 3; ++k) {
+        const double dx = xs[k] - px, dy = ys[k] - py;
+        const double chord = sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+        // signed path length: negative before the perigee in the direction of motion
+        const double sign = __dadd_rn(__dmul_rn(dx, tx), __dmul_rn(dy, ty)) >= 0.0 ? 1.0 : -1.0;
+        if (straight) {
+            s[k] = sign * chord;
+        } else {
+            double a = chord / (2.0 * R);
+            a = a > 1.0 ? 1.0 : a;
+            s[k] = sign * (2.0 * R * asin(a));
+        }
+    }
+    const double sbar = (s[0] + s[1] + s[2]) / 3.0;
+    const double zbar = (zs[0] + zs[1] + zs[2]) / 3.0;
+    double sss = 0.0, ssz = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        sss = __dadd_rn(sss, __dmul_rn(s[k] - sbar, s[k] - sbar));
+        ssz = __dadd_rn(ssz, __dmul_rn(s[k] - sbar, zs[k] - zbar));
+    }
+    if (sss == 0.0)
+        return kFit64Degenerate;
+    const double cot = ssz / sss;
+    const double z0 = __dsub_rn(zbar, __dmul_rn(cot, sbar));
+    par[0] = phi0;
+    par[1] = qopt;
+    par[2] = d0;
+    par[3] = cot;
+    par[4] = z0;
+    uint32_t idx[5];
+    for (int k = 0; k < 5; ++k)
+        if (!bin_f64(C, k, par[k], idx[k]))
+            return 0;
+    bin = idx[0] * C.stride[0] + idx[1] * C.stride[1] + idx[2] * C.stride[2] +
+          idx[3] * C.stride[3] + idx[4];
+    return kFit64Accepted;
+}
+
+// ---------------------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Largest f with off[f] <= x for a non-decreasing off[0..n] (off[0] <= x < off[n]).
+__device__ __forceinline__ int upper_index(const int64_t *off, int n, int64_t x)
+{
+    int lo = 0, hi = n;   // invariant off[lo] <= x < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= x)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+}  // namespace trk

@@ -1,0 +1,876 @@
+// The steps around the vote kernel: packing hits per layer, scheduling work items, the
+// local-maximum peak finder, candidate emission and hit assignment (paper Sec. 7 and
+// Fig. 3: candidates are local maxima of the accumulated parameter space; Sec. 8: the
+// whole event, the parameter space and the peak detection stay resident on the GPU, and
+// the hits of each candidate go on to a fit).
+#include "trk_common.cuh"
+
+namespace trk {
+
+// ---------------------------------------------------------------------------------------
+// a1: pack -- validate, then a stable counting sort of each event's hits by layer into
+// float4 (x, y, z, input index bits); the event keeps its input index range.
+// ---------------------------------------------------------------------------------------
+
+constexpr int kPackThreads = 256;
+
+__global__ void __launch_bounds__(kPackThreads) k_pack(const CallArgs *args, int L, int max_per_event,
+                                                       float4 *packed, int32_t *lay_off,
+                                                       int64_t *ev_begin, int32_t *status)
+{
+    constexpr int NW = kPackThreads / kWarp;
+    __shared__ int cnt[TRK_MAX_LAYERS];
+    __shared__ int base[TRK_MAX_LAYERS];
+    __shared__ int wcnt[NW][TRK_MAX_LAYERS];
+    __shared__ int woff[NW][TRK_MAX_LAYERS];
+    __shared__ int bad;
+    const int e = blockIdx.x;
+    if (e >= args->n_events)
+        return;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int64_t n = args->n_hits;
+    const int64_t a = args->offsets[e], b = args->offsets[e + 1];
+    int32_t *lo = lay_off + (size_t)e * (L + 1);
+    int st = 0;
+    if (!(a >= 0 && a <= b && b <= n))
+        st = TRK_EV_BAD_OFFSETS;
+    else if (b - a > max_per_event)
+        st = TRK_EV_TOO_MANY_HITS;
+    if (st) {
+        for (int l = tid; l <= L; l += kPackThreads)
+            lo[l] = 0;
+        if (tid == 0) {
+            status[e] = st;
+            ev_begin[e] = 0;
+        }
+        return;
+    }
+    for (int l = tid; l < TRK_MAX_LAYERS; l += kPackThreads) {
+        cnt[l] = 0;
+        for (int q = 0; q < NW; ++q)
+            wcnt[q][l] = 0;
+    }
+    if (tid == 0)
+        bad = 0;
+    __syncthreads();
+    const trk_hit *hits = args->hits;
+    for (int64_t h = a + tid; h < b; h += kPackThreads) {
+        const trk_hit x = hits[h];
+        if (x.layer < 0 || x.layer >= L || !isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z))
+            bad = 1;
+        else
+            atomicAdd(&cnt[x.layer], 1);
+    }
+    __syncthreads();
+    if (bad) {
+        for (int l = tid; l <= L; l += kPackThreads)
+            lo[l] = 0;
+        if (tid == 0) {
+            status[e] = TRK_EV_BAD_HIT;
+            ev_begin[e] = 0;
+        }
+        return;
+    }
+    if (tid == 0) {
+        int run = (int)a;
+        for (int l = 0; l < L; ++l) {
+            lo[l] = run;
+            base[l] = run;
+            run += cnt[l];
+        }
+        lo[L] = run;
+        status[e] = 0;
+        ev_begin[e] = a;
+    }
+    __syncthreads();
+    for (int64_t c0 = a; c0 < b; c0 += kPackThreads) {
+        const int64_t h = c0 + tid;
+        trk_hit x;
+        int layer = -1;
+        if (h < b) {
+            x = hits[h];
+            layer = x.layer;
+        }
+        const unsigned peers = __match_any_sync(kFull, layer);
+        const int rank = __popc(peers & lanemask_lt());
+        if (layer >= 0 && lane == __ffs(peers) - 1)
+            wcnt[w][layer] = __popc(peers);
+        __syncthreads();
+        if (tid < L) {
+            int run = base[tid];
+            for (int q = 0; q < NW; ++q) {
+                woff[q][tid] = run;
+                run += wcnt[q][tid];
+                wcnt[q][tid] = 0;
+            }
+            base[tid] = run;
+        }
+        __syncthreads();
+        if (layer >= 0)
+            packed[woff[w][layer] + rank] = make_float4(x.x, x.y, x.z, __int_as_float((int)h));
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// a2: schedule -- work items per (event, layer triple) and their prefix sum
+// ---------------------------------------------------------------------------------------
+
+constexpr int kSchedThreads = 1024;
+
+__global__ void __launch_bounds__(kSchedThreads) k_schedule(const CallArgs *args, const DevGeo *geo,
+                                                            const int32_t *lay_off,
+                                                            const int32_t *status, int ti, int tj,
+                                                            int64_t *item_off, Counters *ctr)
+{
+    __shared__ int64_t warp_sum[kSchedThreads / kWarp];
+    __shared__ int64_t carry;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int T = geo->n_triples, L1 = geo->n_layers + 1;
+    const int F = args->n_events * T;
+    if (tid == 0)
+        carry = 0;
+    unsigned long long trip = 0;
+    __syncthreads();
+    for (int f0 = 0; f0 < F; f0 += kSchedThreads) {
+        const int f = f0 + tid;
+        int64_t items = 0;
+        if (f < F) {
+            const int e = f / T, t = f - (f / T) * T;
+            if (status[e] == 0) {
+                const int32_t *lo = lay_off + (size_t)e * L1;
+                const int la = geo->triples[t][0], lb = geo->triples[t][1], lc = geo->triples[t][2];
+                const int64_t na = lo[la + 1] - lo[la], nb = lo[lb + 1] - lo[lb],
+                              nc = lo[lc + 1] - lo[lc];
+                if (na > 0 && nb > 0 && nc > 0) {
+                    items = ((na + ti - 1) / ti) * ((nb + tj - 1) / tj);
+                    trip += (unsigned long long)(na * nb * nc);
+                }
+            }
+        }
+        // block exclusive scan of items
+        int64_t v = items;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(kFull, v, o);
+            if (lane >= o)
+                v += u;
+        }
+        if (lane == 31)
+            warp_sum[w] = v;
+        __syncthreads();
+        if (w == 0) {
+            int64_t s = warp_sum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t u = __shfl_up_sync(kFull, s, o);
+                if (lane >= o)
+                    s += u;
+            }
+            warp_sum[lane] = s;
+        }
+        __syncthreads();
+        const int64_t before = carry + (w > 0 ? warp_sum[w - 1] : 0) + v - items;
+        if (f < F)
+            item_off[f] = before;
+        __syncthreads();
+        if (tid == kSchedThreads - 1)
+            carry = before + items;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        item_off[F] = carry;
+        ctr->n_items = (unsigned long long)carry;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        trip += __shfl_xor_sync(kFull, trip, o);
+    if (lane == 0 && trip)
+        atomicAdd(&ctr->n_triplets, trip);
+}
+
+// ---------------------------------------------------------------------------------------
+// a5: peaks.  Key of a bin: (count << 32) | ~bin.  A bin satisfies the rule (count >= all
+// neighbours, > the neighbours with a smaller number) iff its key is the strict maximum of
+// the keys of its 3^5 neighbourhood; the maximum over the box is separable.  Pass 1 takes
+// the maximum over (d0, cot, z0) in shared memory, pass 2 over (phi0, q/pT) and compares.
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t key_of(int32_t h, uint32_t lin)
+{
+    return ((uint64_t)(uint32_t)h << 32) | (uint64_t)(~lin);
+}
+
+__device__ __forceinline__ uint64_t max3(uint64_t a, uint64_t b, uint64_t c)
+{
+    const uint64_t m = a > b ? a : b;
+    return m > c ? m : c;
+}
+
+// In-place max over {i-1, i, i+1} along a line of n elements with the given stride.
+__device__ __forceinline__ void line_max3(uint64_t *p, int n, int stride)
+{
+    uint64_t prev = 0, cur = p[0];
+    for (int i = 0; i < n; ++i) {
+        const uint64_t next = (i + 1 < n) ? p[(i + 1) * stride] : 0;
+        p[i * stride] = max3(prev, cur, next);
+        prev = cur;
+        cur = next;
+    }
+}
+
+constexpr int kPeakThreads = 256;
+
+__global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist, uint64_t *m3,
+                                                             FitConst C, int g0, int td,
+                                                             const int32_t *status)
+{
+    extern __shared__ uint64_t sk[];
+    const int n0 = C.n[0], n1 = C.n[1], n2 = C.n[2], n3 = C.n[3], n4 = C.n[4];
+    const int P4 = n4 + 1;
+    const int nslab = (n2 + td - 1) / td;
+    int b = blockIdx.x;
+    const int slab = b % nslab;
+    b /= nslab;
+    const int i1 = b % n1;
+    b /= n1;
+    const int i0 = b % n0;
+    const int ge = b / n0;
+    const int e = g0 + ge;
+    if (status[e] != 0)
+        return;
+    const int tid = threadIdx.x;
+    const int d_start = slab * td;
+    const int rows = min(td, n2 - d_start);
+    const int plane = n3 * n4;
+    const int32_t *h_e = hist + (size_t)e * C.nbins;
+    const uint32_t base = (uint32_t)i0 * C.stride[0] + (uint32_t)i1 * C.stride[1];
+    const int total = (rows + 2) * plane;
+    for (int x = tid; x < total; x += kPeakThreads) {
+        const int lr = x / plane, rem = x - lr * plane;
+        const int i3 = rem / n4, i4 = rem - i3 * n4;
+        const int d = d_start + lr - 1;
+        uint64_t key = 0;
+        if (d >= 0 && d < n2) {
+            const uint32_t lin = base + (uint32_t)d * C.stride[2] + (uint32_t)rem;
+            key = key_of(h_e[lin], lin);
+        }
+        sk[(lr * n3 + i3) * P4 + i4] = key;
+    }
+    __syncthreads();
+    for (int line = tid; line < (rows + 2) * n3; line += kPeakThreads)
+        line_max3(sk + line * P4, n4, 1);
+    __syncthreads();
+    for (int line = tid; line < (rows + 2) * n4; line += kPeakThreads) {
+        const int lr = line / n4, i4 = line - lr * n4;
+        line_max3(sk + lr * n3 * P4 + i4, n3, P4);
+    }
+    __syncthreads();
+    uint64_t *out = m3 + (size_t)ge * C.nbins + base + (uint32_t)d_start * C.stride[2];
+    const int rs = n3 * P4;
+    for (int line = tid; line < plane; line += kPeakThreads) {
+        const int i3 = line / n4, i4 = line - i3 * n4;
+        const uint64_t *p = sk + i3 * P4 + i4;
+        uint64_t prev = p[0], cur = p[rs];
+        for (int r = 0; r < rows; ++r) {
+            const uint64_t next = p[(r + 2) * rs];
+            out[(size_t)r * plane + line] = max3(prev, cur, next);
+            prev = cur;
+            cur = next;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist, const uint64_t *m3,
+                                                             FitConst C, int g0, int G,
+                                                             int threshold, const int32_t *status,
+                                                             uint32_t *cbits, int64_t W)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int n0 = C.n[0], n1 = C.n[1];
+    const bool per0 = (C.periodic & 1) != 0;
+    for (int64_t gw = warp0; gw < (int64_t)G * W; gw += nwarps) {
+        const int ge = (int)(gw / W);
+        const int64_t wi = gw - (int64_t)ge * W;
+        const int e = g0 + ge;
+        bool cand = false;
+        const uint32_t bin = (uint32_t)(wi * 32 + lane);
+        if (status[e] == 0 && bin < C.nbins) {
+            const int32_t h = hist[(size_t)e * C.nbins + bin];
+            if (h >= threshold) {
+                const uint32_t i0 = bin / C.stride[0];
+                const uint32_t r0 = bin - i0 * C.stride[0];
+                const uint32_t i1 = r0 / C.stride[1];
+                const uint32_t rest = r0 - i1 * C.stride[1];
+                const uint64_t *m = m3 + (size_t)ge * C.nbins;
+                uint64_t mx = 0;
+                for (int d0 = -1; d0 <= 1; ++d0) {
+                    int j0 = (int)i0 + d0;
+                    if (j0 < 0 || j0 >= n0) {
+                        if (!per0)
+                            continue;
+                        j0 = (j0 + n0) % n0;
+                    }
+                    for (int d1 = -1; d1 <= 1; ++d1) {
+                        const int j1 = (int)i1 + d1;
+                        if (j1 < 0 || j1 >= n1)
+                            continue;
+                        const uint64_t v = m[(uint32_t)j0 * C.stride[0] + (uint32_t)j1 * C.stride[1] + rest];
+                        mx = v > mx ? v : mx;
+                    }
+                }
+                cand = (mx == key_of(h, bin));
+            }
+        }
+        const unsigned word = __ballot_sync(kFull, cand);
+        if (lane == 0)
+            cbits[(size_t)e * W + wi] = word;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// device-wide exclusive scan (3 kernels), values produced by a functor
+// ---------------------------------------------------------------------------------------
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanPerThread = 4;
+constexpr int kScanBlock = kScanThreads * kScanPerThread;
+
+template <class V>
+__device__ __forceinline__ int64_t block_exclusive_scan(V val, int64_t start, int64_t n,
+                                                        int64_t out_vals[kScanPerThread],
+                                                        int64_t *warp_tot)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int64_t loc[kScanPerThread];
+    int64_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanPerThread; ++q) {
+        const int64_t i = start + (int64_t)tid * kScanPerThread + q;
+        loc[q] = i < n ? val(i) : 0;
+        s += loc[q];
+    }
+    int64_t v = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t u = __shfl_up_sync(kFull, v, o);
+        if (lane >= o)
+            v += u;
+    }
+    if (lane == 31)
+        warp_tot[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int64_t t = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(kFull, t, o);
+            if (lane >= o)
+                t += u;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    int64_t run = (w > 0 ? warp_tot[w - 1] : 0) + v - s;
+#pragma unroll
+    for (int q = 0; q < kScanPerThread; ++q) {
+        out_vals[q] = run;
+        run += loc[q];
+    }
+    const int64_t total = warp_tot[31];
+    __syncthreads();
+    return total;
+}
+
+template <class V, class OutT>
+__global__ void __launch_bounds__(kScanThreads) k_scan_local(V val, const unsigned long long *n_dev,
+                                                             int64_t n_host, int64_t n_cap,
+                                                             OutT *out, int64_t *bsum)
+{
+    __shared__ int64_t warp_tot[32];
+    int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    n = n < n_cap ? n : n_cap;
+    const int64_t start = (int64_t)blockIdx.x * kScanBlock;
+    if (start >= n) {
+        if (threadIdx.x == 0)
+            bsum[blockIdx.x] = 0;
+        return;
+    }
+    int64_t ex[kScanPerThread];
+    const int64_t tot = block_exclusive_scan(val, start, n, ex, warp_tot);
+#pragma unroll
+    for (int q = 0; q < kScanPerThread; ++q) {
+        const int64_t i = start + (int64_t)threadIdx.x * kScanPerThread + q;
+        if (i < n)
+            out[i] = (OutT)ex[q];
+    }
+    if (threadIdx.x == 0)
+        bsum[blockIdx.x] = tot;
+}
+
+struct ArrayVal {
+    const int64_t *a;
+    __device__ int64_t operator()(int64_t i) const { return a[i]; }
+};
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_bsum(int64_t *bsum, int nb,
+                                                            unsigned long long *total_out)
+{
+    __shared__ int64_t warp_tot[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0)
+        carry = 0;
+    __syncthreads();
+    for (int s0 = 0; s0 < nb; s0 += kScanBlock) {
+        int64_t ex[kScanPerThread];
+        const int64_t tot = block_exclusive_scan(ArrayVal{bsum}, s0, nb, ex, warp_tot);
+        const int64_t c = carry;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kScanPerThread; ++q) {
+            const int64_t i = s0 + (int64_t)threadIdx.x * kScanPerThread + q;
+            if (i < nb)
+                bsum[i] = ex[q] + c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            carry = c + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total_out)
+        *total_out = (unsigned long long)carry;
+}
+
+template <class OutT>
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(OutT *out, const int64_t *bsum,
+                                                           const unsigned long long *n_dev,
+                                                           int64_t n_host, int64_t n_cap)
+{
+    int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    n = n < n_cap ? n : n_cap;
+    const int64_t start = (int64_t)blockIdx.x * kScanBlock;
+    if (start >= n || blockIdx.x == 0)
+        return;
+    const int64_t add = bsum[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < kScanPerThread; ++q) {
+        const int64_t i = start + (int64_t)threadIdx.x * kScanPerThread + q;
+        if (i < n)
+            out[i] = (OutT)((int64_t)out[i] + add);
+    }
+}
+
+template <class V, class OutT>
+static cudaError_t scan_exclusive(V val, const unsigned long long *n_dev, int64_t n_host,
+                                  int64_t n_cap, OutT *out, int64_t *bsum,
+                                  unsigned long long *total_out, cudaStream_t s)
+{
+    const int64_t nb64 = (n_cap + kScanBlock - 1) / kScanBlock;
+    const int nb = (int)(nb64 > 0 ? nb64 : 1);
+    k_scan_local<V, OutT><<<nb, kScanThreads, 0, s>>>(val, n_dev, n_host, n_cap, out, bsum);
+    k_scan_bsum<<<1, kScanThreads, 0, s>>>(bsum, nb, total_out);
+    k_scan_add<OutT><<<nb, kScanThreads, 0, s>>>(out, bsum, n_dev, n_host, n_cap);
+    return cudaGetLastError();
+}
+
+struct PopcVal {
+    const uint32_t *w;
+    __device__ int64_t operator()(int64_t i) const { return __popc(w[i]); }
+};
+struct CandVotes3 {
+    const trk_candidate *c;
+    __device__ int64_t operator()(int64_t i) const { return 3 * (int64_t)c[i].votes; }
+};
+struct CandHits {
+    const int32_t *nh;
+    __device__ int64_t operator()(int64_t i) const { return nh[i]; }
+};
+struct ChunkCount {
+    const int32_t *cnt;
+    __device__ int64_t operator()(int64_t i) const { return cnt[i] > 0 ? cnt[i] : 0; }
+};
+
+// ---------------------------------------------------------------------------------------
+// candidates, assignment, compaction
+// ---------------------------------------------------------------------------------------
+
+__global__ void k_cand_emit(const uint32_t *cbits, const uint32_t *wprefix, int64_t n_words,
+                            int64_t W, const int32_t *hist, FitConst C, trk_candidate *cand,
+                            int32_t *fill, int64_t cand_cap, Counters *ctr)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t gw = warp0; gw < n_words; gw += nwarps) {
+        const uint32_t word = cbits[gw];
+        if (word == 0)
+            continue;
+        if ((word >> lane) & 1u) {
+            const int e = (int)(gw / W);
+            const uint32_t bin = (uint32_t)((gw - (int64_t)e * W) * 32 + lane);
+            const int64_t c = (int64_t)wprefix[gw] + __popc(word & lanemask_lt());
+            if (c < cand_cap) {
+                trk_candidate r;
+                r.bin = bin;
+                r.event = e;
+                r.votes = hist[(size_t)e * C.nbins + bin];
+                r.n_hits = 0;
+                r.hit_off = 0;
+                r.reserved = 0;
+                uint32_t rem = bin;
+                for (int k = 0; k < 5; ++k) {
+                    const uint32_t idx = rem / C.stride[k];
+                    rem -= idx * C.stride[k];
+                    const double centre =
+                        __dadd_rn(C.lo_d[k], __dmul_rn((double)idx + 0.5, C.w_d[k]));
+                    r.params[k] = __double2float_rn(centre);
+                }
+                cand[c] = r;
+                fill[c] = 0;
+            } else {
+                atomicOr(&ctr->overflow, 1ull);
+            }
+        }
+    }
+}
+
+// Locates a work item: event, layer triple and the first packed hit of each tile.
+struct ItemLoc {
+    int e, a_first, b_first, c_first;
+};
+
+__device__ __forceinline__ ItemLoc locate_item(int64_t item, const int64_t *item_off, int F, int T,
+                                               const DevGeo *geo, const int32_t *lay_off, int ti,
+                                               int tj)
+{
+    const int f = upper_index(item_off, F, item);
+    const int e = f / T, t = f - e * T;
+    const int L1 = geo->n_layers + 1;
+    const int32_t *lo = lay_off + (size_t)e * L1;
+    const int la = geo->triples[t][0], lb = geo->triples[t][1], lc = geo->triples[t][2];
+    const int nb = lo[lb + 1] - lo[lb];
+    const int64_t local = item - item_off[f];
+    const int ntj = (nb + tj - 1) / tj;
+    const int ti_ = (int)(local / ntj), tj_ = (int)(local - (int64_t)ti_ * ntj);
+    ItemLoc r;
+    r.e = e;
+    r.a_first = lo[la] + ti_ * ti;
+    r.b_first = lo[lb] + tj_ * tj;
+    r.c_first = lo[lc];
+    return r;
+}
+
+
+
+__global__ void k_assign_fill(AssignArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t n_chunks = (int64_t)A.ctr->n_chunks;
+    n_chunks = n_chunks < A.chunk_cap ? n_chunks : A.chunk_cap;
+    const int T = A.geo->n_triples;
+    const int F = A.args->n_events * T;
+    for (int64_t cid = warp0; cid < n_chunks; cid += nwarps) {
+        const int item = A.chunk_item[cid];
+        const int count = A.chunk_count[cid];
+        if (item < 0 || count <= 0)
+            continue;
+        const ItemLoc loc = locate_item(item, A.item_off, F, T, A.geo, A.lay_off, A.ti, A.tj);
+        if (lane >= count)
+            continue;
+        const uint64_t v = A.votes[cid * kWarp + lane];
+        const uint32_t bin = (uint32_t)v;
+        const uint32_t code = (uint32_t)(v >> 32);
+        const size_t wpos = (size_t)loc.e * A.W + (bin >> 5);
+        const uint32_t word = A.cbits[wpos];
+        if (!((word >> (bin & 31)) & 1u))
+            continue;
+        const int64_t c = (int64_t)A.wprefix[wpos] + __popc(word & ((1u << (bin & 31)) - 1u));
+        if (c >= A.cand_cap)
+            continue;
+        const int slot = atomicAdd(&A.fill[c], 1);
+        const int64_t pos = A.vote_off[c] + 3 * (int64_t)slot;
+        if (pos + 3 > A.assign_cap) {
+            atomicOr(&A.ctr->overflow, 2ull);
+            continue;
+        }
+        const uint32_t pair = code >> 24, kl = code & 0xffffffu;
+        const int ip = loc.a_first + (int)(pair / A.tj);
+        const int jp = loc.b_first + (int)(pair % A.tj);
+        const int kp = loc.c_first + (int)kl;
+        const int64_t eb = A.ev_begin[loc.e];
+        A.assign[pos] = __float_as_int(A.packed[ip].w) - (int)eb;
+        A.assign[pos + 1] = __float_as_int(A.packed[jp].w) - (int)eb;
+        A.assign[pos + 2] = __float_as_int(A.packed[kp].w) - (int)eb;
+    }
+}
+
+// Warp per candidate: bitmap over the event's hits -> sorted unique event-local ids,
+// written back over the candidate's own assignment region.
+__global__ void k_cand_hits(const trk_candidate *cand, const unsigned long long *n_cand_dev,
+                            int64_t cand_cap, const int64_t *vote_off, int32_t *assign,
+                            int64_t assign_cap, const CallArgs *args, int32_t *nhits,
+                            int max_words)
+{
+    extern __shared__ uint32_t bm_all[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t *bm = bm_all + (size_t)w * max_words;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t n = (int64_t)*n_cand_dev;
+    n = n < cand_cap ? n : cand_cap;
+    for (int64_t c = warp0; c < n; c += nwarps) {
+        const trk_candidate r = cand[c];
+        const int64_t ne = args->offsets[r.event + 1] - args->offsets[r.event];
+        const int words = (int)((ne + 31) / 32);
+        const int64_t off = vote_off[c];
+        int64_t m = 3 * (int64_t)r.votes;
+        if (off + m > assign_cap)
+            m = 0;
+        for (int q = lane; q < words; q += 32)
+            bm[q] = 0;
+        __syncwarp();
+        for (int64_t q = lane; q < m; q += 32) {
+            const int id = assign[off + q];
+            if ((unsigned)id < (unsigned)ne)
+                atomicOr(&bm[id >> 5], 1u << (id & 31));
+        }
+        __syncwarp();
+        int64_t run = 0;
+        for (int q0 = 0; q0 < words; q0 += 32) {
+            const int q = q0 + lane;
+            uint32_t word = q < words ? bm[q] : 0u;
+            const int pc = __popc(word);
+            int inc = pc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o)
+                    inc += u;
+            }
+            int64_t pos = off + run + inc - pc;
+            while (word) {
+                const int bit = __ffs(word) - 1;
+                word &= word - 1;
+                assign[pos++] = q * 32 + bit;
+            }
+            run += __shfl_sync(kFull, inc, 31);
+        }
+        if (lane == 0)
+            nhits[c] = (int32_t)run;
+        __syncwarp();
+    }
+}
+
+__global__ void k_compact(trk_candidate *cand, const unsigned long long *n_cand_dev, int64_t cand_cap,
+                          const int64_t *vote_off, const int32_t *assign, const int32_t *nhits,
+                          const int64_t *hit_off, const int64_t *ev_begin, int32_t *hit_ids)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t n = (int64_t)*n_cand_dev;
+    n = n < cand_cap ? n : cand_cap;
+    for (int64_t c = warp0; c < n; c += nwarps) {
+        const int e = cand[c].event;
+        const int64_t src = vote_off[c], dst = hit_off[c];
+        const int k = nhits[c];
+        const int eb = (int)ev_begin[e];
+        for (int q = lane; q < k; q += 32)
+            hit_ids[dst + q] = assign[src + q] + eb;
+        if (lane == 0) {
+            cand[c].hit_off = dst;
+            cand[c].n_hits = k;
+        }
+    }
+}
+
+// Per-event candidate offsets and the call's verdict.
+__global__ void k_finalize(const uint32_t *wprefix, int64_t W, const CallArgs *args, Counters *ctr,
+                           int64_t cand_cap, int64_t *cand_off, int32_t *status)
+{
+    const int n_events = args->n_events;
+    const unsigned long long ncand = ctr->n_cand;
+    const bool over = ctr->overflow != 0 || ncand > (unsigned long long)cand_cap;
+    for (int e = threadIdx.x; e <= n_events; e += blockDim.x) {
+        int64_t v = e < n_events ? (int64_t)wprefix[(size_t)e * W] : (int64_t)ncand;
+        cand_off[e] = over ? 0 : v;
+        if (over && e < n_events)
+            status[e] |= TRK_EV_CAND_OVERFLOW;
+    }
+}
+
+// Decode the vote list into (event, i, j, k) input indices and bins (debug helper).
+__global__ void k_decode_votes(AssignArgs A, const int64_t *chunk_pos, int64_t n_chunks,
+                               int32_t *dst, uint32_t *bins, int64_t cap)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int T = A.geo->n_triples;
+    const int F = A.args->n_events * T;
+    for (int64_t cid = warp0; cid < n_chunks; cid += nwarps) {
+        const int item = A.chunk_item[cid];
+        const int count = A.chunk_count[cid];
+        if (item < 0 || count <= 0)
+            continue;
+        const ItemLoc loc = locate_item(item, A.item_off, F, T, A.geo, A.lay_off, A.ti, A.tj);
+        if (lane >= count)
+            continue;
+        const int64_t out = chunk_pos[cid] + lane;
+        if (out >= cap)
+            continue;
+        const uint64_t v = A.votes[cid * kWarp + lane];
+        const uint32_t code = (uint32_t)(v >> 32);
+        const uint32_t pair = code >> 24, kl = code & 0xffffffu;
+        dst[4 * out] = loc.e;
+        dst[4 * out + 1] = __float_as_int(A.packed[loc.a_first + (int)(pair / A.tj)].w);
+        dst[4 * out + 2] = __float_as_int(A.packed[loc.b_first + (int)(pair % A.tj)].w);
+        dst[4 * out + 3] = __float_as_int(A.packed[loc.c_first + (int)kl].w);
+        bins[out] = (uint32_t)v;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+
+// Raise the dynamic shared-memory limits once (outside any stream capture).
+cudaError_t prepare_pipeline_kernels()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_peak_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_cand_hits, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024);
+}
+
+cudaError_t launch_pack(const CallArgs *args, int n_events, int L, int max_per_event,
+                        float4 *packed, int32_t *lay_off, int64_t *ev_begin, int32_t *status,
+                        cudaStream_t s)
+{
+    k_pack<<<n_events, kPackThreads, 0, s>>>(args, L, max_per_event, packed, lay_off, ev_begin,
+                                             status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_schedule(const CallArgs *args, const DevGeo *geo, const int32_t *lay_off,
+                            const int32_t *status, int ti, int tj, int64_t *item_off,
+                            Counters *ctr, cudaStream_t s)
+{
+    k_schedule<<<1, kSchedThreads, 0, s>>>(args, geo, lay_off, status, ti, tj, item_off, ctr);
+    return cudaGetLastError();
+}
+
+size_t peak_pass1_smem(const FitConst &C, int td)
+{
+    return sizeof(uint64_t) * (size_t)(td + 2) * C.n[3] * (C.n[4] + 1);
+}
+
+cudaError_t launch_peaks(const int32_t *hist, uint64_t *m3, const FitConst &C, int g0, int G,
+                         int td, int threshold, const int32_t *status, uint32_t *cbits,
+                         int64_t W, int n_sm, cudaStream_t s)
+{
+    const size_t sm = peak_pass1_smem(C, td);
+    const int nslab = (C.n[2] + td - 1) / td;
+    const int64_t grid1 = (int64_t)G * C.n[0] * C.n[1] * nslab;
+    k_peak_pass1<<<(unsigned)grid1, kPeakThreads, sm, s>>>(hist, m3, C, g0, td, status);
+    const int64_t words = (int64_t)G * W;
+    int64_t grid2 = (words + (kPeakThreads / 32) - 1) / (kPeakThreads / 32);
+    const int64_t cap2 = (int64_t)n_sm * 16;
+    grid2 = grid2 < cap2 ? grid2 : cap2;
+    k_peak_pass2<<<(unsigned)(grid2 > 0 ? grid2 : 1), kPeakThreads, 0, s>>>(
+        hist, m3, C, g0, G, threshold, status, cbits, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_word_scan(const uint32_t *cbits, int64_t n_words, uint32_t *wprefix,
+                             int64_t *bsum, unsigned long long *total, cudaStream_t s)
+{
+    return scan_exclusive(PopcVal{cbits}, nullptr, n_words, n_words, wprefix, bsum, total, s);
+}
+
+cudaError_t launch_cand_emit(const uint32_t *cbits, const uint32_t *wprefix, int64_t n_words,
+                             int64_t W, const int32_t *hist, const FitConst &C,
+                             trk_candidate *cand, int32_t *fill, int64_t cand_cap, Counters *ctr,
+                             int n_sm, cudaStream_t s)
+{
+    int64_t grid = (n_words + 7) / 8;
+    const int64_t cap = (int64_t)n_sm * 16;
+    grid = grid < cap ? grid : cap;
+    k_cand_emit<<<(unsigned)(grid > 0 ? grid : 1), 256, 0, s>>>(cbits, wprefix, n_words, W, hist,
+                                                                 C, cand, fill, cand_cap, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vote_offsets(const trk_candidate *cand, const unsigned long long *n_cand,
+                                int64_t cand_cap, int64_t *vote_off, int64_t *bsum,
+                                unsigned long long *total, cudaStream_t s)
+{
+    return scan_exclusive(CandVotes3{cand}, n_cand, 0, cand_cap, vote_off, bsum, total, s);
+}
+
+cudaError_t launch_assign(const AssignArgs &A, int n_sm, cudaStream_t s)
+{
+    k_assign_fill<<<n_sm * 16, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cand_hits(const trk_candidate *cand, const unsigned long long *n_cand,
+                             int64_t cand_cap, const int64_t *vote_off, int32_t *assign,
+                             int64_t assign_cap, const CallArgs *args, int32_t *nhits,
+                             int max_words, int n_sm, cudaStream_t s)
+{
+    int warps = (int)((96 * 1024) / ((size_t)max_words * 4));
+    warps = warps < 1 ? 1 : (warps > 8 ? 8 : warps);
+    const size_t sm = (size_t)warps * max_words * 4;
+    k_cand_hits<<<n_sm * 8, warps * 32, sm, s>>>(cand, n_cand, cand_cap, vote_off, assign,
+                                                  assign_cap, args, nhits, max_words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hit_offsets(const int32_t *nhits, const unsigned long long *n_cand,
+                               int64_t cand_cap, int64_t *hit_off, int64_t *bsum,
+                               unsigned long long *total, cudaStream_t s)
+{
+    return scan_exclusive(CandHits{nhits}, n_cand, 0, cand_cap, hit_off, bsum, total, s);
+}
+
+cudaError_t launch_compact(trk_candidate *cand, const unsigned long long *n_cand, int64_t cand_cap,
+                           const int64_t *vote_off, const int32_t *assign, const int32_t *nhits,
+                           const int64_t *hit_off, const int64_t *ev_begin, int32_t *hit_ids,
+                           int n_sm, cudaStream_t s)
+{
+    k_compact<<<n_sm * 8, 256, 0, s>>>(cand, n_cand, cand_cap, vote_off, assign, nhits, hit_off,
+                                        ev_begin, hit_ids);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const uint32_t *wprefix, int64_t W, const CallArgs *args,
+                            Counters *ctr, int64_t cand_cap, int64_t *cand_off, int32_t *status,
+                            cudaStream_t s)
+{
+    k_finalize<<<1, 256, 0, s>>>(wprefix, W, args, ctr, cand_cap, cand_off, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_positions(const int32_t *chunk_count, int64_t n_chunks, int64_t *pos,
+                                   int64_t *bsum, unsigned long long *total, cudaStream_t s)
+{
+    return scan_exclusive(ChunkCount{chunk_count}, nullptr, n_chunks, n_chunks, pos, bsum, total,
+                          s);
+}
+
+cudaError_t launch_decode_votes(const AssignArgs &A, const int64_t *chunk_pos, int64_t n_chunks,
+                                int32_t *dst, uint32_t *bins, int64_t cap, int n_sm,
+                                cudaStream_t s)
+{
+    k_decode_votes<<<n_sm * 8, 256, 0, s>>>(A, chunk_pos, n_chunks, dst, bins, cap);
+    return cudaGetLastError();
+}
+
+}  // namespace trk

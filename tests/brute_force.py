@@ -2,7 +2,8 @@
 
 It shares nothing with the C oracle: the circle comes from the linear system
 x^2 + y^2 + E x + F y + G = 0 (numpy.linalg.solve), the sense of motion from the order of
-the polar angles about the centre, arc lengths from the angle swept about the centre,
+the polar angles about the centre, signed path lengths from the angle swept about the
+centre in the sense of motion (negative before the perigee),
 the longitudinal line from numpy.polyfit, bin indices from numpy.searchsorted on
 numpy.linspace edges, and the enumeration walks every ordered triple of distinct hits,
 keeping those whose layers form a listed layer triple.
@@ -33,7 +34,8 @@ def helix(p1, p2, p3, b_tesla):
         foot = P[0][:2] - np.dot(P[0][:2], t) * t
         phi0 = math.atan2(t[1], t[0])
         d0 = -foot[0] * math.sin(phi0) + foot[1] * math.cos(phi0)
-        s = np.array([np.hypot(*(p[:2] - foot)) for p in P])
+        # signed distance along the direction of motion
+        s = np.array([np.dot(p[:2] - foot, t) for p in P])
         qopt = 0.0
     else:
         E, F, G = np.linalg.solve(A, rhs)
@@ -53,8 +55,9 @@ def helix(p1, p2, p3, b_tesla):
         thp = math.atan2(foot[1] - c[1], foot[0] - c[0])
         s = []
         for t_ in th:
+            # angle swept from the perigee in the sense of motion, in (-pi, pi]
             dth = (t_ - thp + math.pi) % (2 * math.pi) - math.pi
-            s.append(R * abs(dth))
+            s.append(R * (dth if ccw else -dth))
         s = np.array(s)
     z = np.array([p[2] for p in P])
     if np.ptp(s) == 0.0:

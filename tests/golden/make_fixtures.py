@@ -7,7 +7,8 @@ test: it imports neither the oracle nor the CUDA library.
   hand_triplets.json -- helix-from-triplet worked examples.  Sec. 8 of the paper: a circle
       is fixed by its centre and radius; readings: pT = K B R, K = 0.299792458e-2
       GeV/(T cm), positive charges turn clockwise seen from +z, perigee about the origin,
-      z = z0 + s cot(theta) with s the arc length from the perigee.
+      z = z0 + s cot(theta) with s the signed path length from the perigee (negative for
+      a hit the particle passes before reaching the perigee).
   peak_rule.json -- hand-built 5-D histograms for the local-maximum rule (Sec. 7 and
       Fig. 3 of the paper: candidates are local maxima of the parameter space).
 
@@ -59,6 +60,22 @@ def hand_triplets():
         b_tesla=B, hits=[[-24.0, 18.0, z0 + cot * s[0]], [-32.0, 26.0, z0 + cot * s[1]],
                          [-40.0, 50.0, z0 + cot * s[2]]],
         expected=[math.pi, 1.0 / (K * B * R), -10.0, cot, z0], arc_lengths=s))
+    # hits on both sides of the perigee: circle centre (0, 25), radius 25, through the origin
+    R = 25.0
+    th1 = 2.0 * math.asin(math.sqrt(50.0) / 50.0)     # |p1 - P| = sqrt(7^2 + 1^2)
+    th3 = 2.0 * math.asin(30.0 / 50.0)                # |p3 - P| = sqrt(24^2 + 18^2) = 30
+    s = [-R * th1, R * th1, R * th3]
+    cot, z0 = 0.5, 2.0
+    cases.append(dict(
+        name="hits_before_and_after_perigee",
+        derivation="Circle centre (0,25), radius 25 through the origin: (-7,1), (7,1), (24,18) lie on "
+                   "it. Their angles about the centre increase (-106.3, -73.7, -16.3 degrees): "
+                   "counter-clockwise, negative charge, P = (0,0), tangent +x, phi0 = 0, d0 = 0. The "
+                   "first hit comes before the perigee: s = -2R asin(sqrt(50)/50), then "
+                   "+2R asin(sqrt(50)/50), +2R asin(30/50); z = 2 + 0.5 s.",
+        b_tesla=B, hits=[[-7.0, 1.0, z0 + cot * s[0]], [7.0, 1.0, z0 + cot * s[1]],
+                         [24.0, 18.0, z0 + cot * s[2]]],
+        expected=[0.0, -1.0 / (K * B * R), 0.0, cot, z0], arc_lengths=s))
     cases.append(dict(
         name="straight_through_origin",
         derivation="(3,4), (6,8), (9,12) are exactly collinear (D = 0): q/pT = 0, direction "
