@@ -203,7 +203,41 @@ int trk_fit_triplets(trk_ctx *h, const trk_hit *hits, int64_t n_hits, const int3
  * ms[4] hit assignment, compaction and the result copies; ms[5..7] = 0.  Synchronises. */
 int trk_profile_stages(trk_ctx *h, float ms[8], void *stream);
 
-/* Text of the last error on this handle (or of the last failed trk_create if h NULL). */
+/* Largest histogram, in bins per event, that trk_find_peaks_noalloc accepts. */
+#define TRK_NOALLOC_MAX_BINS (1 << 21)
+
+/* Candidate bins of dense vote histograms, for callers that may not allocate device memory.
+ * The paper has no counterpart: this is a deployment variant of the peak step.
+ *
+ * Who needs it: code that must never call cudaMalloc (or any allocating library routine)
+ * while it runs -- a trigger path with a fixed latency budget where an allocation could
+ * stall, a process whose device memory is all handed out up front by its own pool, a
+ * plug-in that is given device buffers by a host framework and may not own any.  Such a
+ * caller cannot create a trk handle (trk_create allocates its pools) but may hold vote
+ * histograms.  This function applies the candidate rule of trk_reconstruct to them and
+ * allocates nothing: the peak filter's scratch (8 bytes per bin) is a static device array
+ * of the library, 16 MiB, present on every GPU that loads the library until the process
+ * exits.
+ *
+ * hist: DEVICE int32, n_events dense histograms of the binning's size, row-major (as
+ * trk_get_histogram writes them); cand_bits: DEVICE uint32, n_events x ceil(bins / 32)
+ * words, bit b of event e set iff bin b is a candidate; both owned by the caller.  Runs on
+ * `stream` (a cudaStream_t; NULL = legacy default stream), asynchronously.
+ * Returns TRK_ERR_INVALID (nothing launched) for null pointers, n_events < 1, an invalid
+ * binning, or more than TRK_NOALLOC_MAX_BINS bins; TRK_ERR_CUDA on a launch failure.
+ * trk_last_error(NULL) gives the reason.
+ *
+ * The first call on a device sets that device up (looks up the static array's device
+ * address with cudaGetSymbolAddress and sets kernel attributes): make that first call
+ * outside any stream capture.  Every call on a device uses the same array, which keeps
+ * the last call's contents (each call writes every entry it reads, so no clearing is
+ * needed); calls whose work overlaps on the GPU (other streams, other threads) race on
+ * it and must be serialized by the caller. */
+int trk_find_peaks_noalloc(const int32_t *hist, int32_t n_events, const trk_binning *binning,
+                           uint32_t *cand_bits, void *stream);
+
+/* Text of the last error on this handle (h NULL: of the last failed trk_create or
+ * trk_find_peaks_noalloc). */
 const char *trk_last_error(const trk_ctx *h);
 
 /* Library version string. */

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtrk.so")
-SOURCES = ["trk_vote.cu", "trk_pipeline.cu", "trk_api.cu"]
+SOURCES = ["trk_vote.cu", "trk_pipeline.cu", "trk_api.cu", "trk_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

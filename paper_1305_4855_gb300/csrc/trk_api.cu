@@ -64,6 +64,11 @@ using namespace trk;
 
 static std::string g_create_error;
 
+namespace trk {
+// Message for trk_last_error(NULL), from handle-free entry points.
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace trk
+
 struct trk_ctx {
     int device = 0;
     int n_sm = 0;

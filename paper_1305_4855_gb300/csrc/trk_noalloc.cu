@@ -1,0 +1,155 @@
+// trk_find_peaks_noalloc: the local-maximum peak finder for callers that cannot allocate
+// device memory.
+//
+// Some callers must not call cudaMalloc at all: code running where an allocation could
+// block or fail at an unpredictable moment (a trigger path with a fixed latency budget,
+// a process that hands out all device memory up front through its own pool, a plug-in
+// that receives device buffers from a host framework and may not own any).  Such a caller
+// cannot create a trk handle (trk_create allocates every pool), but it may already hold
+// dense vote histograms.  This entry point runs the same two peak kernels as
+// trk_reconstruct on them; the kernels' only scratch (the per-bin maximum of the keys over
+// (d0, cot, z0), 8 bytes per bin) lives in the static device array below, so nothing is
+// allocated: not by this file, not by the CUDA runtime on its behalf, not by torch.
+//
+// Costs and limits of that choice:
+//   * the array takes 16 MiB of device memory on every GPU that loads the library, until
+//     the process exits, whether or not this entry point is used;
+//   * a histogram may have at most TRK_NOALLOC_MAX_BINS (2^21) bins;
+//   * all calls share the one array, so two calls whose work overlaps on the GPU (on
+//     different streams, or from different host threads) race and corrupt each other's
+//     results; serialize them.  The array keeps the last call's contents; every bin a call
+//     reads is written earlier in that same call, so nothing needs clearing between calls.
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "trk_common.cuh"
+
+namespace trk {
+size_t peak_pass1_smem(const FitConst &C, int td);
+cudaError_t launch_peaks(const int32_t *hist, uint64_t *m3, const FitConst &C, int g0, int G,
+                         int td, int threshold, const int32_t *status, uint32_t *cbits,
+                         int64_t W, int n_sm, cudaStream_t s);
+cudaError_t prepare_pipeline_kernels();
+void set_global_error(const std::string &msg);
+}  // namespace trk
+
+using namespace trk;
+
+// The peak finder's scratch, shared by every call on a device.
+static __device__ __align__(256) uint64_t g_peak_scratch[TRK_NOALLOC_MAX_BINS];
+// Per-event status read by the peak kernels: always zero (never written).
+static __device__ __align__(256) int32_t g_zero_status[1];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+struct DeviceSetup {
+    bool ready = false;
+    uint64_t *scratch = nullptr;   // device address of g_peak_scratch
+    int32_t *zero = nullptr;       // device address of g_zero_status
+    int n_sm = 0;
+};
+
+std::mutex g_setup_mutex;
+DeviceSetup g_setup[kMaxDevices];
+
+int noalloc_fail(int code, const std::string &msg)
+{
+    set_global_error(msg);
+    return code;
+}
+
+// Once per device, with that device current: the device addresses of the static arrays
+// (host code only sees host-side stand-ins for their names) and the kernels' shared-memory
+// limit.
+int setup_device(int dev, DeviceSetup **out)
+{
+    if (dev < 0 || dev >= kMaxDevices)
+        return noalloc_fail(TRK_ERR_INVALID, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    DeviceSetup &d = g_setup[dev];
+    if (!d.ready) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_peak_scratch);
+        if (e != cudaSuccess)
+            return noalloc_fail(TRK_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") +
+                                                  cudaGetErrorString(e));
+        d.scratch = static_cast<uint64_t *>(p);
+        e = cudaGetSymbolAddress(&p, g_zero_status);
+        if (e != cudaSuccess)
+            return noalloc_fail(TRK_ERR_CUDA, std::string("cudaGetSymbolAddress(status): ") +
+                                                  cudaGetErrorString(e));
+        d.zero = static_cast<int32_t *>(p);
+        e = prepare_pipeline_kernels();
+        if (e != cudaSuccess)
+            return noalloc_fail(TRK_ERR_CUDA, std::string("kernel attributes: ") +
+                                                  cudaGetErrorString(e));
+        e = cudaDeviceGetAttribute(&d.n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess || d.n_sm < 1)
+            return noalloc_fail(TRK_ERR_CUDA, "multiprocessor count unavailable");
+        d.ready = true;
+    }
+    *out = &d;
+    return TRK_OK;
+}
+
+}  // namespace
+
+extern "C" int trk_find_peaks_noalloc(const int32_t *hist, int32_t n_events,
+                                      const trk_binning *binning, uint32_t *cand_bits,
+                                      void *stream)
+{
+    if (!hist || !binning || !cand_bits || n_events < 1)
+        return noalloc_fail(TRK_ERR_INVALID, "null pointer or n_events < 1");
+    double nb = 1.0;
+    for (int k = 0; k < 5; ++k) {
+        if (binning->n[k] < 1 || !(binning->lo[k] < binning->hi[k]))
+            return noalloc_fail(TRK_ERR_INVALID, "invalid binning dimension");
+        nb *= binning->n[k];
+    }
+    if (nb > (double)TRK_NOALLOC_MAX_BINS)
+        return noalloc_fail(TRK_ERR_INVALID,
+                            "histogram larger than TRK_NOALLOC_MAX_BINS (2^21 bins): use a "
+                            "trk handle (trk_reconstruct), whose scratch is allocated");
+    if (binning->periodic & ~1)
+        return noalloc_fail(TRK_ERR_INVALID, "only dimension 0 (phi0) may be periodic");
+    if (binning->threshold < 1)
+        return noalloc_fail(TRK_ERR_INVALID, "threshold must be >= 1");
+    if ((double)binning->n[3] * (binning->n[4] + 1) * 8.0 * 3.0 > 200.0 * 1024.0)
+        return noalloc_fail(TRK_ERR_INVALID, "n[3] * (n[4] + 1) too large for the filter tile");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return noalloc_fail(TRK_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    DeviceSetup *d = nullptr;
+    const int rc = setup_device(dev, &d);
+    if (rc != TRK_OK)
+        return rc;
+
+    // the bin layout the peak kernels read (the rest of FitConst is unused by them)
+    FitConst C;
+    memset(&C, 0, sizeof(C));
+    uint32_t stride = 1;
+    for (int k = 4; k >= 0; --k) {
+        C.stride[k] = stride;
+        stride *= (uint32_t)binning->n[k];
+        C.n[k] = binning->n[k];
+    }
+    C.nbins = (uint32_t)nb;
+    C.periodic = binning->periodic;
+    const int64_t W = ((int64_t)C.nbins + 31) / 32;
+    int td = binning->n[2];
+    while (td > 1 && peak_pass1_smem(C, td) > 200 * 1024)
+        --td;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int ev = 0; ev < n_events; ++ev) {
+        e = launch_peaks(hist + (size_t)ev * C.nbins, d->scratch, C, 0, 1, td,
+                         binning->threshold, d->zero, cand_bits + (size_t)ev * W, W, d->n_sm, s);
+        if (e != cudaSuccess)
+            return noalloc_fail(TRK_ERR_CUDA, std::string("peak kernels: ") +
+                                                  cudaGetErrorString(e));
+    }
+    return TRK_OK;
+}

@@ -24,7 +24,8 @@ TRK_EV_CAND_OVERFLOW, TRK_EV_BAD_OFFSETS = 8, 16
 
 EXPORTED = ["trk_options_default", "trk_create", "trk_reconstruct", "trk_reconstruct_host",
             "trk_destroy", "trk_get_stats", "trk_get_histogram", "trk_histogram_size",
-            "trk_get_votes", "trk_fit_triplets", "trk_profile_stages", "trk_last_error", "trk_version"]
+            "trk_get_votes", "trk_fit_triplets", "trk_profile_stages", "trk_last_error", "trk_version",
+            "trk_find_peaks_noalloc"]
 
 
 class trk_geometry(C.Structure):
@@ -107,6 +108,8 @@ def load_library(path: str = LIB_PATH):
     lib.trk_profile_stages.restype = C.c_int
     lib.trk_last_error.argtypes = [vp]
     lib.trk_last_error.restype = C.c_char_p
+    lib.trk_find_peaks_noalloc.argtypes = [vp, i32, C.POINTER(trk_binning), vp, vp]
+    lib.trk_find_peaks_noalloc.restype = C.c_int
     lib.trk_version.argtypes = []
     lib.trk_version.restype = C.c_char_p
     _lib = lib
