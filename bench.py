@@ -28,10 +28,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "barrel10_500trk"
-# FP32 operations of the curvature prefilter evaluated for every enumerated triplet
-# (4 differences, 3 multiply + 3 fused products for D, |v|^2, |w|^2, 3 products and one
-# comparison), the unit of the vote kernel's algorithmic work.
-PREFILTER_OPS = 14
+BATCH_WORKLOAD = "barrel10_batch256"
+# Algorithmic FP32 work of the vote kernel, counted from its formulas (add, multiply,
+# fused multiply-add, compare each 1; square root, division, arcsine, arctangent each 1):
+#   every enumerated triplet: the curvature test (4 differences, D, |v|^2, |w|^2, 3 products,
+#     1 comparison) = 14;
+#   every survivor of it: the transverse fit (circle, q/pT, d0, perigee) = 62 and the
+#     conservative longitudinal bound (truncated arcsine series, interval least squares) = 181;
+#   every survivor of the bound: the transverse fit again (62), the exact longitudinal fit
+#     (signed arc lengths, least-squares line) = 124, phi0 and the five bin indices = 41.
+OPS_PER_TRIPLET = 14
+OPS_PER_FIT = 62 + 181
+OPS_PER_EXACT = 62 + 124 + 41
 
 
 def parse():
@@ -43,6 +51,10 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-variants", action="store_true",
+                   help="skip the batched / plain-on-batch / served measurements")
+    p.add_argument("--batch-events", type=int, default=256)
+    p.add_argument("--serve-seconds", type=float, default=12.0)
     return p.parse_args()
 
 
@@ -230,6 +242,7 @@ def main():
     hits = torch.from_numpy(batch.packed()).cuda()
     offs = torch.from_numpy(batch.offsets).cuda()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    tuning = rec.autotune(hits, offs, reps=2, stream=stream)
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):
             rc = rec.reconstruct_device(hits, offs, stream=stream)
@@ -280,7 +293,8 @@ def main():
     sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
     # FP32 lane-operation peak: 128 FP32 lanes per SM per clock
     alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12
-    alg_ops = (PREFILTER_OPS * stats["n_triplets"]) / 1e12
+    alg_ops = (OPS_PER_TRIPLET * stats["n_triplets"] + OPS_PER_FIT * stats["n_fit"] +
+               OPS_PER_EXACT * stats["n_exact"]) / 1e12
     achieved = alg_ops / (vote_ms / 1000.0) if vote_ms else None
     line = {
         "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world,
@@ -289,33 +303,161 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "events_per_step": 1, "hits_per_event": batch.n_hits,
                    "triplets_per_event": n_trip, "bins": rec.lib.trk_histogram_size(rec.h),
-                   "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas"},
+                   "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas",
+                   "tuning": tuning},
         "hit_triplets_per_s": value * n_trip,
-        "stats": {k: stats[k] for k in ("n_triplets", "n_fit", "n_votes", "n_fp64", "n_candidates",
+        "stats": {k: stats[k] for k in ("n_triplets", "n_fit", "n_exact", "n_votes", "n_fp64", "n_candidates",
                                         "n_hit_ids", "n_work_items")},
         "roofline": {"bound": "alu", "kernel": "k_vote", "achieved": achieved, "peak": alu_peak,
                      "unit": "TFLOP/s", "frac": (achieved / alu_peak) if achieved else None,
                      "traffic": None, "vote_kernel_ms": vote_ms,
                      "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (median SM clock under load)"
                                    % (sm_count, sm_mhz),
-                     "achieved_basis": "%d FP32 ops of the curvature test per enumerated triplet"
-                                       % PREFILTER_OPS},
+                     "achieved_basis": "%d FP32 ops per enumerated triplet + %d per fit + %d per "
+                                       "exact fit (vote kernel stats of the call)"
+                                       % (OPS_PER_TRIPLET, OPS_PER_FIT, OPS_PER_EXACT)},
         "e2e": {"value": world * args.steps / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "stage_ms": stage_ms,
         "clocks": clocks,
         "gpu_launches": args.steps * LAUNCHES_PER_CALL,
     }
+    rec.close()
+    if not args.no_variants:
+        line["variants"] = run_variants(args, local)
     if rank == 0 and not args.no_cpu_baseline:
         trip_s, cores, sample = cpu_baseline(cfg, batch, args.cpu_seconds)
         line["cpu_baseline"] = {"value": trip_s / n_trip, "unit": "events/s", "cores": cores,
                                 "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    rec.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_variants(args, local):
+    """Batched (one call per memory-sized sub-batch of the 256-event uneven workload),
+    the same events through the plain path one call each, and served (Poisson arrivals
+    through the continuous-batching server).  Device-resident inputs for the first two,
+    host inputs (the server's own copies) for the third."""
+    import torch
+    from paper_1305_4855_gb300 import events as ev
+    from paper_1305_4855_gb300.trk import Reconstructor, Server
+    cfg = ev.load_workload(BATCH_WORKLOAD)
+    batch = ev.make_batch(cfg, n_events=args.batch_events)
+    n_trip = int(ev.layer_triplet_count(batch, cfg["geometry"]["triples"]).sum())
+    out = {}
+    # --- batched: sub-batches of SUB events, each one trk_reconstruct (one graph launch)
+    sub = 32
+    per_event_max = int(np.diff(batch.offsets).max())
+    rec = Reconstructor(cfg, max_events=sub, max_hits=sub * per_event_max, device=local,
+                        vote_capacity=1 << 32, cand_capacity=1 << 23, assign_capacity=1 << 28,
+                        peak_scratch_bytes=8 << 30)
+    packed = torch.from_numpy(batch.packed()).cuda()
+    chunks = []
+    for s0 in range(0, batch.n_events, sub):
+        s1 = min(batch.n_events, s0 + sub)
+        a, b_ = int(batch.offsets[s0]), int(batch.offsets[s1])
+        chunks.append((packed[a:b_].contiguous(),
+                       torch.from_numpy(batch.offsets[s0:s1 + 1] - a).cuda()))
+    stream = torch.cuda.Stream()
+    tuning = rec.autotune(chunks[0][0], chunks[0][1], reps=1, stream=stream)
+    with torch.cuda.stream(stream):
+        for h_, o_ in chunks[:1]:
+            rec.reconstruct_device(h_, o_, stream=stream)
+    torch.cuda.synchronize()
+    st_ev, en_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    failed = 0
+    with torch.cuda.stream(stream):
+        st_ev.record(stream)
+        for h_, o_ in chunks:
+            rc = rec.reconstruct_device(h_, o_, stream=stream)
+            failed += int(rc != 0)
+        en_ev.record(stream)
+    torch.cuda.synchronize()
+    ms = st_ev.elapsed_time(en_ev)
+    out["batched"] = {"workload": BATCH_WORKLOAD, "events": batch.n_events, "sub_batch": sub,
+                      "events_per_s": batch.n_events / (ms / 1000.0),
+                      "hit_triplets_per_s": n_trip / (ms / 1000.0), "ms": ms,
+                      "calls_with_capacity_errors": failed, "tuning": tuning}
+    rec.close()
+    # --- the same events through the plain path, one call per event
+    rec = Reconstructor(cfg, max_events=1, max_hits=per_event_max, device=local,
+                        vote_capacity=1 << 29, cand_capacity=1 << 21, assign_capacity=1 << 25)
+    evs = [(packed[int(batch.offsets[e]):int(batch.offsets[e + 1])].contiguous(),
+            torch.tensor([0, int(batch.offsets[e + 1] - batch.offsets[e])], dtype=torch.int64,
+                         device="cuda")) for e in range(batch.n_events)]
+    rec.autotune(evs[0][0], evs[0][1], reps=1, stream=stream)
+    with torch.cuda.stream(stream):
+        rec.reconstruct_device(evs[0][0], evs[0][1], stream=stream)
+    torch.cuda.synchronize()
+    lat = []
+    with torch.cuda.stream(stream):
+        st_ev.record(stream)
+        for h_, o_ in evs:
+            t0 = time.perf_counter()
+            rec.reconstruct_device(h_, o_, stream=stream)
+            lat.append(time.perf_counter() - t0)
+        en_ev.record(stream)
+    torch.cuda.synchronize()
+    ms = st_ev.elapsed_time(en_ev)
+    out["plain_on_batch_events"] = {"events_per_s": batch.n_events / (ms / 1000.0),
+                                    "hit_triplets_per_s": n_trip / (ms / 1000.0), "ms": ms,
+                                    "p50_ms": 1000 * float(np.percentile(lat, 50)),
+                                    "p99_ms": 1000 * float(np.percentile(lat, 99))}
+    rec.close()
+    # --- served: open-loop Poisson arrivals (a prefix of the 1e6-event stream)
+    out["served"] = run_served(args, cfg, batch, out["batched"]["events_per_s"], local)
+    return out
+
+
+def run_served(args, cfg, batch, capacity, local):
+    from paper_1305_4855_gb300.trk import Server
+    per_event_max = int(np.diff(batch.offsets).max())
+    hosts = [batch.packed()[int(batch.offsets[e]):int(batch.offsets[e + 1])]
+             for e in range(batch.n_events)]
+    res = {}
+    rates = {"at_0.8_capacity": 0.8 * capacity,
+             "offered_100kHz": float(cfg.get("serving", {}).get("arrival_rate_hz", 100000.0))}
+    serving_cfg = dict(cfg)
+    for name, rate in rates.items():
+        srv = Server(serving_cfg, lane_events=8, lane_hits=8 * per_event_max, n_lanes=2,
+                     device=local, vote_capacity=1 << 31, cand_capacity=1 << 21,
+                     assign_capacity=1 << 26)
+        # warm both lanes (graph capture) outside the measurement
+        for t in [srv.submit(hosts[0]), srv.submit(hosts[1])]:
+            srv.wait(t, 120.0)
+        rng = np.random.default_rng(5)
+        duration = args.serve_seconds / 2
+        # the same number of events in both runs (what 80 % of capacity delivers in
+        # `duration`); at the offered 100 kHz they arrive ~1000x faster than they can be
+        # served, so the queue, and with it the latency, grows over the run
+        n_max = int(0.8 * capacity * duration) + 1
+        gaps = rng.exponential(1.0 / rate, n_max)
+        tickets = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for i in range(n_max):
+            t_next += gaps[i]
+            now = time.perf_counter()
+            if t_next > now:
+                time.sleep(t_next - now)
+            tickets.append(srv.submit(hosts[i % len(hosts)]))
+        lats, nb = [], []
+        for t in tickets:
+            info = srv.wait(t, 600.0)
+            lats.append(info["latency_s"])
+            nb.append(info["batch_events"])
+        wall = time.perf_counter() - t0
+        res[name] = {"offered_hz": rate, "events": len(tickets), "events_per_s": len(tickets) / wall,
+                     "p50_ms": 1000 * float(np.percentile(lats, 50)),
+                     "p99_ms": 1000 * float(np.percentile(lats, 99)),
+                     "p999_ms": 1000 * float(np.percentile(lats, 99.9)),
+                     "mean_batch_events": float(np.mean(nb)), "lanes": 2,
+                     "note": "prefix of the 1e6-event stream: the first %d events" % len(tickets)}
+        srv.close()
+    return res
 
 
 # kernels of one trk_reconstruct call for a one-event batch: pack, schedule, vote,

@@ -48,6 +48,7 @@ extern "C" {
 #define TRK_ERR_CAPACITY (-2) /* some event exceeded a capacity; see the per-event status */
 #define TRK_ERR_CUDA (-3)     /* a CUDA call failed; trk_last_error() has the text */
 #define TRK_ERR_NOMEM (-4)    /* device or pinned-host allocation failed */
+#define TRK_PENDING (-5)      /* served event not finished yet (trk_server_wait / _take) */
 
 /* per-event status bits (an event with a non-zero status has no candidates: like a
  * problematic event in the filter farm, it is passed on unprocessed) */
@@ -100,6 +101,8 @@ typedef struct trk_options {
     int32_t k_chunk;                        /* outer-layer hits staged per shared chunk */
     int32_t blocks_per_sm;                  /* persistent vote blocks per SM (0: auto) */
     int32_t use_graph;                      /* capture each call shape in a CUDA graph */
+    int32_t vote_level;                     /* vote kernel occupancy: 2, 3 or 4 blocks of 256
+                                               threads per SM (0: 3) */
 } trk_options;
 
 /* One candidate (48 bytes). */
@@ -134,7 +137,8 @@ typedef struct trk_candidates {
 /* Counters of the last call. */
 typedef struct trk_stats {
     int64_t n_triplets;                     /* sum over events and triples of |La||Lb||Lc| */
-    int64_t n_fit;                          /* triplets through the full FP32 fit */
+    int64_t n_fit;                          /* triplets through the transverse FP32 fit */
+    int64_t n_exact;                        /* triplets through the exact longitudinal fit */
     int64_t n_votes;                        /* accepted triplets */
     int64_t n_fp64;                         /* fits redone in FP64 */
     int64_t n_candidates;
@@ -175,6 +179,20 @@ int trk_destroy(trk_ctx *h);
 /* Counters of the last call. */
 int trk_get_stats(trk_ctx *h, trk_stats *out);
 
+/* Vote-kernel configuration chosen by trk_autotune. */
+typedef struct trk_tuning {
+    int32_t tile_i, tile_j;                 /* pair tile of a block */
+    int32_t vote_level;                     /* occupancy level (blocks of 256 threads / SM) */
+    float vote_ms;                          /* mean vote-kernel time of the winner */
+} trk_tuning;
+
+/* Autotuner: reconstructs the given events (DEVICE buffers, as trk_reconstruct) reps + 1
+ * times with every supported vote-kernel tile and occupancy level, keeps the one whose
+ * vote kernel is fastest (the results do not depend on the choice) and reports it.
+ * Later calls use it; cached graphs are dropped.  Synchronises. */
+int trk_autotune(trk_ctx *h, const trk_hit *hits, int64_t n_hits, const int64_t *event_offsets,
+                 int32_t n_events, int32_t reps, trk_tuning *best, void *stream);
+
 /* Copy event e's dense vote histogram of the last call (n bins int32, row-major) to the
  * DEVICE buffer dst, on `stream`. */
 int trk_get_histogram(trk_ctx *h, int32_t event, int32_t *dst, void *stream);
@@ -202,6 +220,49 @@ int trk_fit_triplets(trk_ctx *h, const trk_hit *hits, int64_t n_hits, const int3
  * histogram clear, packing and scheduling, ms[2] the peak finder, ms[3] candidate emission,
  * ms[4] hit assignment, compaction and the result copies; ms[5..7] = 0.  Synchronises. */
 int trk_profile_stages(trk_ctx *h, float ms[8], void *stream);
+
+/* ---- serving: continuous batching of events that arrive one at a time ------------------
+ * The paper's filter unit takes one event after another and overlaps the next event's
+ * transfer with the current one's processing (Sec. 8).  A server keeps n_lanes complete
+ * handles resident (each with its own pools, stream and graphs, created with
+ * lane_options) and a host queue of submitted events.  Each lane runs on its own host
+ * thread: when free, it admits every waiting event that fits its capacities
+ * (lane_options.max_events events, lane_options.max_hits hits), reconstructs them in one
+ * call and files each event's candidates; lanes overlap on the GPU.  An event's results
+ * are identical whether it is reconstructed alone, in a batch or by the server. */
+typedef struct trk_server trk_server;
+
+typedef struct trk_served_event {
+    int32_t status;                         /* TRK_EV_* bits of the event (-1: call failed) */
+    int32_t rc;                             /* return code of the lane's reconstruction */
+    double latency_s;                       /* submit -> results on the host */
+    int32_t batch_events;                   /* events reconstructed in the same call */
+    int64_t n_candidates;
+    int64_t n_hit_ids;
+} trk_served_event;
+
+/* Create a server of n_lanes (1..16) lanes; each lane allocates one trk handle. */
+int trk_server_create(trk_server **out, const trk_geometry *geometry, const trk_binning *binning,
+                      const trk_options *lane_options, int32_t n_lanes);
+
+/* Queue one event (HOST hits, copied before returning); *ticket identifies it.
+ * TRK_ERR_CAPACITY if it has more hits than a lane accepts. */
+int trk_server_submit(trk_server *s, const trk_hit *hits, int64_t n_hits, uint64_t *ticket);
+
+/* Wait up to timeout_s seconds (0: do not wait) for an event; TRK_PENDING if not done. */
+int trk_server_wait(trk_server *s, uint64_t ticket, double timeout_s, trk_served_event *out);
+
+/* Copy a finished event's candidates (hit_off into hit_ids, event 0) and its hit ids
+ * (event-local indices, sorted per candidate) to HOST buffers and forget the event. */
+int trk_server_take(trk_server *s, uint64_t ticket, trk_candidate *cand, int64_t cand_cap,
+                    int32_t *hit_ids, int64_t hit_cap);
+
+/* Batches run, events finished, events whose call or status failed, events waiting. */
+int trk_server_counts(trk_server *s, int64_t *n_batches, int64_t *n_events, int64_t *n_failed,
+                      int64_t *n_queued);
+
+/* Stop the lanes (finishing queued events) and free everything.  NULL is accepted. */
+int trk_server_destroy(trk_server *s);
 
 /* Largest histogram, in bins per event, that trk_find_peaks_noalloc accepts. */
 #define TRK_NOALLOC_MAX_BINS (1 << 21)

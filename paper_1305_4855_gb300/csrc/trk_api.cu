@@ -10,10 +10,11 @@
 #include "trk_common.cuh"
 
 namespace trk {
-cudaError_t launch_vote(const VoteArgs &A, int ti, int tj, int grid, cudaStream_t s);
-cudaError_t vote_occupancy(int ti, int tj, int *blocks);
+cudaError_t launch_vote(const VoteArgs &A, int ti, int tj, int level, int grid, cudaStream_t s);
+cudaError_t vote_occupancy(int ti, int tj, int level, int *blocks);
 bool vote_tile_supported(int ti, int tj);
-cudaError_t prepare_vote_kernel(int ti, int tj);
+bool vote_level_supported(int level);
+cudaError_t prepare_vote_kernel(int ti, int tj, int level);
 cudaError_t prepare_pipeline_kernels();
 cudaError_t launch_fit_triplets(const trk_hit *hits, int64_t n_hits, const int32_t *ijk,
                                 int64_t n, const FitConst &C, float *params, uint32_t *bins,
@@ -77,7 +78,7 @@ struct trk_ctx {
     trk_options opt;
     FitConst C;
     int64_t nbins = 0, W = 0;
-    int td = 0, group = 1, vote_grid = 0, max_words = 0;
+    int td = 0, group = 1, vote_grid = 0, max_words = 0, level = 3;
     int64_t chunk_cap = 0, bsum_cap = 0;
 
     DevGeo *d_geo = nullptr;
@@ -92,6 +93,7 @@ struct trk_ctx {
     uint64_t *d_votes = nullptr;
     int32_t *d_chunk_item = nullptr;
     int32_t *d_chunk_count = nullptr;
+    int32_t *d_chunk_event = nullptr;
     uint64_t *d_m3 = nullptr;
     uint32_t *d_cbits = nullptr;
     uint32_t *d_wprefix = nullptr;
@@ -123,6 +125,20 @@ struct trk_ctx {
     int last_n_events = 0;
     std::string err;
 };
+
+// Persistent vote blocks: blocks_per_sm if given, else what the occupancy calculator
+// allows for the instantiation (at least one per SM).
+static int vote_grid_for(int n_sm, int ti, int tj, int level, int blocks_per_sm)
+{
+    int bps = blocks_per_sm;
+    if (bps <= 0) {
+        int occ = 0;
+        if (vote_occupancy(ti, tj, level, &occ) != cudaSuccess || occ < 1)
+            occ = 1;
+        bps = occ;
+    }
+    return n_sm * bps;
+}
 
 static int fail(trk_ctx *h, int code, const std::string &msg)
 {
@@ -156,6 +172,7 @@ extern "C" void trk_options_default(trk_options *o, int32_t max_events, int64_t 
     o->k_chunk = 2048;
     o->blocks_per_sm = 0;
     o->use_graph = 1;
+    o->vote_level = 0;
 }
 
 extern "C" const char *trk_version(void) { return "trk 0.1 (sm_103a)"; }
@@ -245,6 +262,10 @@ static int validate(const trk_geometry *g, const trk_binning *b, const trk_optio
         why = "unsupported tile_i x tile_j";
         return 0;
     }
+    if (o->vote_level != 0 && !vote_level_supported(o->vote_level)) {
+        why = "vote_level must be 0 (default), 2, 3 or 4";
+        return 0;
+    }
     return 1;
 }
 
@@ -252,7 +273,7 @@ static void free_all(trk_ctx *h)
 {
     void *dev[] = {h->d_geo,       h->d_args,       h->d_ctr,         h->d_packed,   h->d_lay_off,
                    h->d_ev_begin,  h->d_status,     h->d_item_off,    h->d_hist,     h->d_votes,
-                   h->d_chunk_item, h->d_chunk_count, h->d_m3,        h->d_cbits,    h->d_wprefix,
+                   h->d_chunk_item, h->d_chunk_count, h->d_chunk_event, h->d_m3,        h->d_cbits,    h->d_wprefix,
                    h->d_bsum,      h->d_cand,       h->d_fill,        h->d_vote_off, h->d_assign,
                    h->d_nhits,     h->d_hit_off,    h->d_hit_ids,     h->d_cand_off, h->d_in_hits,
                    h->d_in_offsets, h->d_chunk_pos};
@@ -315,6 +336,7 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
     std::memset(&C, 0, sizeof(C));
     const double kB = kGeVPerTeslaCm * geometry->b_tesla;
     C.kB = (float)kB;
+    C.inv_kB = (float)(1.0 / kB);
     C.kB_d = kB;
     const double qmax = std::fmax(std::fabs(binning->lo[1]), std::fabs(binning->hi[1]));
     // 4 D^2 <= (kB qmax)^2 |u|^2|v|^2|w|^2, with a 1e-3 relative margin so that the
@@ -341,8 +363,10 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
     C.period0 = C.hi[0] - C.lo[0];
     h->W = (h->nbins + 31) / 32;
     // peak filter: rows per slab and events per group
+    // rows of a peak-filter slab: small enough for 4 resident blocks per SM (halo rows cost
+    // 2/td extra loads)
     int td = binning->n[2];
-    while (td > 1 && peak_pass1_smem(C, td) > 200 * 1024)
+    while (td > 1 && peak_pass1_smem(C, td) > 48 * 1024)
         --td;
     h->td = td;
     int64_t g = o.peak_scratch_bytes / (h->nbins * 8);
@@ -356,14 +380,12 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
         mc = c > mc ? c : mc;
     h->bsum_cap = (mc + 4095) / 4096 + 1;
 
-    int bps = o.blocks_per_sm;
-    if (bps <= 0) {
-        int occ = 0;
-        if (vote_occupancy(o.tile_i, o.tile_j, &occ) != cudaSuccess || occ < 1)
-            occ = 1;
-        bps = occ;
+    h->level = o.vote_level ? o.vote_level : 3;
+    if (prepare_vote_kernel(o.tile_i, o.tile_j, h->level) != cudaSuccess) {
+        delete h;
+        return fail(nullptr, TRK_ERR_CUDA, "vote kernel attributes");
     }
-    h->vote_grid = h->n_sm * bps;
+    h->vote_grid = vote_grid_for(h->n_sm, o.tile_i, o.tile_j, h->level, o.blocks_per_sm);
 
     DevGeo dg;
     std::memset(&dg, 0, sizeof(dg));
@@ -395,6 +417,7 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
     ALLOC(d_votes, h->chunk_cap * 32);
     ALLOC(d_chunk_item, h->chunk_cap);
     ALLOC(d_chunk_count, h->chunk_cap);
+    ALLOC(d_chunk_event, h->chunk_cap);
     ALLOC(d_m3, (int64_t)h->group * h->nbins);
     ALLOC(d_cbits, E * h->W);
     ALLOC(d_wprefix, E * h->W);
@@ -422,7 +445,6 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
         cudaStreamCreate(&h->own_stream) != cudaSuccess ||
         cudaEventCreate(&h->ev_st[0]) != cudaSuccess || cudaEventCreate(&h->ev_st[1]) != cudaSuccess ||
         cudaEventCreate(&h->ev_st[2]) != cudaSuccess || cudaEventCreate(&h->ev_st[3]) != cudaSuccess ||
-        prepare_vote_kernel(o.tile_i, o.tile_j) != cudaSuccess ||
         prepare_pipeline_kernels() != cudaSuccess ||
         cudaMemset(h->d_hist, 0, sizeof(int32_t) * (size_t)(E * h->nbins)) != cudaSuccess ||
         cudaMemset(h->d_chunk_item, 0xff, sizeof(int32_t) * (size_t)h->chunk_cap) != cudaSuccess ||
@@ -476,11 +498,12 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     va.votes = h->d_votes;
     va.chunk_item = h->d_chunk_item;
     va.chunk_count = h->d_chunk_count;
+    va.chunk_event = h->d_chunk_event;
     va.chunk_cap = h->chunk_cap;
     va.ctr = ctr;
     va.C = h->C;
     TRK_CUDA(h, mark(h->ev_st[0]));
-    TRK_CUDA(h, launch_vote(va, o.tile_i, o.tile_j, h->vote_grid, s));
+    TRK_CUDA(h, launch_vote(va, o.tile_i, o.tile_j, h->level, h->vote_grid, s));
     TRK_CUDA(h, mark(h->ev_st[1]));
     for (int g0 = 0; g0 < n_events; g0 += h->group) {
         const int G = (n_events - g0) < h->group ? (n_events - g0) : h->group;
@@ -498,6 +521,7 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     aa.votes = h->d_votes;
     aa.chunk_item = h->d_chunk_item;
     aa.chunk_count = h->d_chunk_count;
+    aa.chunk_event = h->d_chunk_event;
     aa.chunk_cap = h->chunk_cap;
     aa.item_off = h->d_item_off;
     aa.geo = h->d_geo;
@@ -574,6 +598,7 @@ static int finish_call(trk_ctx *h, int n_events, trk_candidates *out, cudaStream
     trk_stats &st = h->stats;
     st.n_triplets = (int64_t)c.n_triplets;
     st.n_fit = (int64_t)c.n_fit;
+    st.n_exact = (int64_t)c.n_exact;
     st.n_votes = (int64_t)c.n_votes;
     st.n_fp64 = (int64_t)c.n_fp64;
     st.n_candidates = over ? 0 : (int64_t)c.n_cand;
@@ -778,5 +803,77 @@ extern "C" int trk_profile_stages(trk_ctx *h, float ms[8], void *stream)
     TRK_CUDA(h, cudaEventElapsedTime(&ms[2], h->ev_st[1], h->ev_st[2]));
     TRK_CUDA(h, cudaEventElapsedTime(&ms[3], h->ev_st[2], h->ev_st[3]));
     TRK_CUDA(h, cudaEventElapsedTime(&ms[4], h->ev_st[3], h->ev1));
+    return TRK_OK;
+}
+
+extern "C" int trk_autotune(trk_ctx *h, const trk_hit *hits, int64_t n_hits,
+                            const int64_t *event_offsets, int32_t n_events, int32_t reps,
+                            trk_tuning *best, void *stream)
+{
+    if (!h || !best || reps < 1)
+        return TRK_ERR_INVALID;
+    static const int tiles[][2] = {{16, 16}, {8, 16}, {16, 8}, {8, 8}, {4, 16}};
+    const int levels[] = {2, 3, 4};
+    trk_tuning cur;
+    std::memset(&cur, 0, sizeof(cur));
+    float best_ms = 1e30f;
+    const trk_options saved = h->opt;
+    const int saved_level = h->level, saved_grid = h->vote_grid;
+    int bti = saved.tile_i, btj = saved.tile_j, blv = saved_level;
+    for (const auto &t : tiles) {
+        for (int lv : levels) {
+            if (prepare_vote_kernel(t[0], t[1], lv) != cudaSuccess)
+                continue;
+            h->opt.tile_i = t[0];
+            h->opt.tile_j = t[1];
+            h->level = lv;
+            h->vote_grid = vote_grid_for(h->n_sm, t[0], t[1], lv, saved.blocks_per_sm);
+            for (auto &kv : h->graphs)
+                cudaGraphExecDestroy(kv.second);
+            h->graphs.clear();
+            float tot = 0.0f;
+            int ok = 1;
+            for (int r = 0; r <= reps && ok; ++r) {
+                const int rc = trk_reconstruct(h, hits, n_hits, event_offsets, n_events, nullptr,
+                                               stream);
+                if (rc != TRK_OK && rc != TRK_ERR_CAPACITY) {
+                    ok = 0;
+                    break;
+                }
+                float ms[8];
+                if (trk_profile_stages(h, ms, stream) != TRK_OK) {
+                    ok = 0;
+                    break;
+                }
+                if (r > 0)
+                    tot += ms[0];
+            }
+            if (ok && tot / reps < best_ms) {
+                best_ms = tot / reps;
+                bti = t[0];
+                btj = t[1];
+                blv = lv;
+            }
+        }
+    }
+    if (best_ms >= 1e29f) {
+        h->opt = saved;
+        h->level = saved_level;
+        h->vote_grid = saved_grid;
+        prepare_vote_kernel(saved.tile_i, saved.tile_j, saved_level);
+        return fail(h, TRK_ERR_CUDA, "autotune: no configuration ran");
+    }
+    h->opt.tile_i = bti;
+    h->opt.tile_j = btj;
+    h->level = blv;
+    h->vote_grid = vote_grid_for(h->n_sm, bti, btj, blv, saved.blocks_per_sm);
+    TRK_CUDA(h, prepare_vote_kernel(bti, btj, blv));
+    for (auto &kv : h->graphs)
+        cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    best->tile_i = bti;
+    best->tile_j = btj;
+    best->vote_level = blv;
+    best->vote_ms = best_ms;
     return TRK_OK;
 }

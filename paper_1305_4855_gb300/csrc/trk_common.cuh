@@ -24,6 +24,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // Constants of the fit and of the binning, passed by value to the kernels.
 struct FitConst {
     float kB;            // K * B [GeV / cm]
+    float inv_kB;        // 1 / (K * B)
     float pre_k2;        // curvature prefilter: 4 D^2 <= pre_k2 * |u|^2 |v|^2 |w|^2
     float sag2;          // FP64 recomputation when D^2 <= sag2 * |v|^2
     int periodic;        // bit 0 only (phi0)
@@ -66,7 +67,8 @@ struct Counters {
     unsigned long long n_assign;     // 3 x votes over candidates
     unsigned long long n_hit_ids;    // assigned hit ids
     unsigned long long overflow;     // bit 0 candidate capacity, bit 1 assignment capacity
-    unsigned long long pad[5];
+    unsigned long long n_exact;      // triplets through the exact longitudinal fit
+    unsigned long long pad[4];
 };
 
 // A run of consecutive votes of one work item in the vote list.
@@ -94,6 +96,7 @@ struct VoteArgs {
     uint64_t *votes;             // [chunk_cap * 32]
     int32_t *chunk_item;         // [chunk_cap] item of each 32-slot chunk (-1: empty)
     int32_t *chunk_count;        // [chunk_cap]
+    int32_t *chunk_event;        // [chunk_cap] event of the chunk's item
     int64_t chunk_cap;
     Counters *ctr;
     FitConst C;
@@ -104,6 +107,7 @@ struct AssignArgs {
     const uint64_t *votes;
     const int32_t *chunk_item;
     const int32_t *chunk_count;
+    const int32_t *chunk_event;
     int64_t chunk_cap;
     const int64_t *item_off;
     const DevGeo *geo;
@@ -168,120 +172,251 @@ __device__ __forceinline__ bool in_range_f32(const FitConst &C, int k, float p)
     return p >= C.lo[k] && p < C.hi[k];
 }
 
-// Everything but phi0 for points p1, p2, p3 (x, y, z in .x .y .z).
-__device__ __forceinline__ int fit_stage_b(const float4 &p1, const float4 &p2, const float4 &p3,
-                                           const FitConst &C, FitB &r)
+// Transverse part of the fit: circle, q/pT, d0 and the perigee.
+struct Trans {
+    float ux, uy, vx, vy, uu, vv;
+    float sgn, qopt, d0;
+    float cpx, cpy;      // centre - p1
+    float cx, cy;        // centre
+    float cn;            // |c|
+    float R, inv2r;
+    float px, py;        // perigee
+};
+
+__device__ __forceinline__ int fit_transverse(const float4 &p1, const float4 &p2,
+                                              const float4 &p3, const FitConst &C, Trans &t)
 {
-    const float ux = p2.x - p1.x, uy = p2.y - p1.y;
-    const float vx = p3.x - p1.x, vy = p3.y - p1.y;
+    t.ux = p2.x - p1.x;
+    t.uy = p2.y - p1.y;
+    t.vx = p3.x - p1.x;
+    t.vy = p3.y - p1.y;
     const float wx = p3.x - p2.x, wy = p3.y - p2.y;
-    const float D = det2(ux, uy, vx, vy);
-    const float uu = fmaf(ux, ux, uy * uy);
-    const float vv = fmaf(vx, vx, vy * vy);
+    const float D = det2(t.ux, t.uy, t.vx, t.vy);
+    t.uu = fmaf(t.ux, t.ux, t.uy * t.uy);
+    t.vv = fmaf(t.vx, t.vx, t.vy * t.vy);
     const float ww = fmaf(wx, wx, wy * wy);
-    if (D * D <= C.sag2 * vv)
+    if (D * D <= C.sag2 * t.vv)
         return kNeedFp64;
     // q/pT = -sign(D) / (K B R), R = |u||v||w| / (2|D|)
-    const float sq = sqrtf(uu * vv * ww);
-    const float qopt = (-2.0f * D) / (C.kB * sq);
-    if (!in_range_f32(C, 1, qopt))
+    const float sq = sqrtf(t.uu * t.vv * ww);
+    const float rq = 1.0f / sq;
+    t.qopt = (-2.0f * D) * rq * C.inv_kB;
+    if (!in_range_f32(C, 1, t.qopt))
         return kReject;
     // centre c = p1 + (v_y|u|^2 - u_y|v|^2, u_x|v|^2 - v_x|u|^2) / (2D)
     const float inv2d = 0.5f / D;
-    const float cpx = det2(vy, uy, vv, uu) * inv2d;
-    const float cpy = det2(ux, vx, uu, vv) * inv2d;
-    const float cx = p1.x + cpx, cy = p1.y + cpy;
-    const float R = sq * fabsf(inv2d);
-    const float cn = sqrtf(fmaf(cx, cx, cy * cy));
+    t.cpx = det2(t.vy, t.uy, t.vv, t.uu) * inv2d;
+    t.cpy = det2(t.ux, t.vx, t.uu, t.vv) * inv2d;
+    t.cx = p1.x + t.cpx;
+    t.cy = p1.y + t.cpy;
+    t.R = sq * fabsf(inv2d);
+    t.inv2r = fabsf(D) * rq;
+    t.cn = sqrtf(fmaf(t.cx, t.cx, t.cy * t.cy));
     // |c| - R = (|c|^2 - R^2) / (|c| + R), |c|^2 - R^2 = |p1|^2 + 2 p1.(c - p1)
-    const float power = fmaf(p1.x, p1.x, p1.y * p1.y) + 2.0f * fmaf(p1.x, cpx, p1.y * cpy);
-    const float dist = power / (cn + R);
-    const float sgn = D > 0.0f ? 1.0f : -1.0f;
-    const float d0 = sgn * dist;
-    if (!in_range_f32(C, 2, d0))
+    const float power = fmaf(p1.x, p1.x, p1.y * p1.y) + 2.0f * fmaf(p1.x, t.cpx, p1.y * t.cpy);
+    const float dist = power / (t.cn + t.R);
+    t.sgn = D > 0.0f ? 1.0f : -1.0f;
+    t.d0 = t.sgn * dist;
+    if (!in_range_f32(C, 2, t.d0))
         return kReject;
-    if (!(cn > 0.0f) || !(R < 3.0e37f))
+    if (!(t.cn > 0.0f) || !(t.R < 3.0e37f))
         return kNeedFp64;
     // perigee P = c (|c| - R) / |c|
-    const float f = dist / cn;
-    const float px = cx * f, py = cy * f;
-    const float inv2r = 0.5f / R;
-    const float twor = 2.0f * R;
-    // Signed path length s_k from P (negative for a hit before P in the direction of
-    // motion).  |s| = 2R asin(chord / 2R) while the chord is short, the sign from the
-    // projection on the direction of motion sgn (c_y, -c_x) / |c|; towards half a turn
-    // (chord -> 2R) the asin form is ill-conditioned in FP32, so there s is R times the
-    // signed central angle between P - c = -R c/|c| and p_k - c, from atan2.
-    const float ax = -R * (cx / cn), ay = -R * (cy / cn);
-    const float bx[3] = {-cpx, ux - cpx, vx - cpx};
-    const float by[3] = {-cpy, uy - cpy, vy - cpy};
-    float s[3];
+    const float f = dist / t.cn;
+    t.px = t.cx * f;
+    t.py = t.cy * f;
+    return kPass;
+}
+
+// Square root and reciprocal through the MUFU approximations (relative error a few 1e-7):
+// used only inside the conservative bound below, whose margins are 1e-4.
+__device__ __forceinline__ float approx_sqrt(float x)
+{
+    return x * rsqrtf(fmaxf(x, 1e-30f));
+}
+__device__ __forceinline__ float approx_rcp(float x) { return __fdividef(1.0f, x); }
+
+// arcsin(x) / x through the x^6 term of its series: 1 + x^2/6 + 3x^4/40 + 5x^6/112.  The
+// remaining terms are positive and below 0.075 x^8 for x <= 0.71 (the ratio of the
+// remainder to x^8 increases with x and is 0.0750 at x = 0.7).
+__device__ __forceinline__ float asin_over_x_series(float x2)
+{
+    return fmaf(x2, fmaf(x2, fmaf(x2, 5.0f / 112.0f, 3.0f / 40.0f), 1.0f / 6.0f), 1.0f);
+}
+
+// Conservative longitudinal test without transcendentals: may the triplet's (cot, z0) be
+// in range?  Each |s_k| is replaced by a truncated arcsine series -- chord / 2R = x <= 0.7:
+// chord (series of x); beyond, the complementary form R (pi - 2 y series(y)) with
+// y = |(P - c) + (p_k - c)| / 2R -- with a rigorous bound on the truncation, a margin for
+// the FP32 evaluation, and interval arithmetic over the least-squares line.  false =
+// certainly outside the cot or z0 range (the exact fit would reject it).
+__device__ __forceinline__ bool z_may_accept(const float4 &p1, const float4 &p2, const float4 &p3,
+                                             const Trans &t, const FitConst &C)
+{
     const float4 *pk[3] = {&p1, &p2, &p3};
+    const float rcn = approx_rcp(t.cn);
+    const float ax = -t.R * t.cx * rcn, ay = -t.R * t.cy * rcn;          // P - c
+    const float bxs[3] = {-t.cpx, t.ux - t.cpx, t.vx - t.cpx};
+    const float bys[3] = {-t.cpy, t.uy - t.cpy, t.vy - t.cpy};
+    float sh[3], E[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float dx = pk[k]->x - px, dy = pk[k]->y - py;
-        const float chord = sqrtf(fmaf(dx, dx, dy * dy));
-        const float x = chord * inv2r;
+        const float dx = pk[k]->x - t.px, dy = pk[k]->y - t.py;
+        const float ch = approx_sqrt(fmaf(dx, dx, dy * dy));
+        const float x = ch * t.inv2r;
+        float mag, e;
         if (x <= 0.7f) {
-            const float m = twor * asinf(x);
-            s[k] = (sgn * det2(dx, dy, cx, cy) >= 0.0f) ? m : -m;
+            const float x2 = x * x, x4 = x2 * x2;
+            mag = ch * asin_over_x_series(x2);
+            e = ch * (0.075f * x4 * x4);
         } else {
-            const float cr = det2(ax, ay, bx[k], by[k]);
-            const float dt = fmaf(ax, bx[k], ay * by[k]);
-            s[k] = sgn * R * atan2f(cr, dt);
+            const float sx = ax + bxs[k], sy = ay + bys[k];
+            const float y = fminf(approx_sqrt(fmaf(sx, sx, sy * sy)) * t.inv2r, 1.0f);
+            const float y2 = y * y, y4 = y2 * y2;
+            mag = t.R * fmaf(-2.0f * y, asin_over_x_series(y2), 3.14159265f);
+            e = 2.0f * t.R * y * (0.075f * y4 * y4);
         }
+        e += fmaf(4e-6f, mag, 1e-6f * t.R);
+        const float pr = det2(dx, dy, t.cx, t.cy);
+        if (fabsf(pr) <= 1e-3f * ch * t.cn)
+            e += 2.0f * mag;                   // direction from P not resolved
+        sh[k] = (t.sgn * pr >= 0.0f) ? mag : -mag;
+        E[k] = e;
     }
-    // The slope needs only differences s_k - s_1; each absolute s_k carries its own
-    // rounding, which a hit with a large z residual and little lever turns into a large
-    // slope error.  The arc a between p1 and p_k from the chord |p_k - p1| (a difference
-    // of inputs) is accurate, and s_k - s_1 is one of a, -a, a - 2 pi R, 2 pi R - a: the
-    // one closest to the difference of the absolute values.
-    float dlt[3];
-    dlt[0] = 0.0f;
-    const float cu = sqrtf(uu), cv = sqrtf(vv);
-    const float turn = 6.2831853f * R;
+    const float zbar = (p1.z + p2.z + p3.z) * (1.0f / 3.0f);
+    const float sbar = (sh[0] + sh[1] + sh[2]) * (1.0f / 3.0f);
+    const float eb = (E[0] + E[1] + E[2]) * (1.0f / 3.0f);
+    const float t0 = sh[0] - sbar, t1 = sh[1] - sbar, t2 = sh[2] - sbar;
+    const float z0d = p1.z - zbar, z1d = p2.z - zbar, z2d = p3.z - zbar;
+    const float d0 = E[0] + eb, d1 = E[1] + eb, d2 = E[2] + eb;   // bound of each |dt_k|
+    const float T = fmaf(t0, t0, fmaf(t1, t1, t2 * t2));
+    const float Z = fmaf(t0, z0d, fmaf(t1, z1d, t2 * z2d));
+    const float dZ = fmaf(d0, fabsf(z0d), fmaf(d1, fabsf(z1d), d2 * fabsf(z2d)));
+    const float nd = approx_sqrt(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
+    const float rt = approx_sqrt(T);
+    if (!(rt > 2.0f * nd))
+        return true;
+    const float tlo = (rt - nd) * (rt - nd), thi = (rt + nd) * (rt + nd);
+    const float zlo = Z - dZ, zhi = Z + dZ;
+    const float rlo = approx_rcp(tlo), rhi = approx_rcp(thi);
+    float clo = fminf(zlo * rlo, zlo * rhi), chi = fmaxf(zhi * rlo, zhi * rhi);
+    // FP32 margin (the exact path's own errors are far below it)
+    const float m3 = 1e-4f * fmaxf(fabsf(clo) + fabsf(chi), C.hi[3] - C.lo[3]);
+    clo -= m3;
+    chi += m3;
+    if (chi < C.lo[3] || clo >= C.hi[3])
+        return false;
+    // z0 = zbar - cot * sbar_true, sbar_true in [sbar - eb, sbar + eb]
+    const float slo = sbar - eb, shi = sbar + eb;
+    const float q0 = clo * slo, q1 = clo * shi, q2 = chi * slo, q3 = chi * shi;
+    const float plo = fminf(fminf(q0, q1), fminf(q2, q3));
+    const float phi = fmaxf(fmaxf(q0, q1), fmaxf(q2, q3));
+    float zlo0 = zbar - phi, zhi0 = zbar - plo;
+    const float m4 = 1e-4f * fmaxf(fabsf(zlo0) + fabsf(zhi0) + fabsf(zbar), C.hi[4] - C.lo[4]);
+    zlo0 -= m4;
+    zhi0 += m4;
+    return !(zhi0 < C.lo[4] || zlo0 >= C.hi[4]);
+}
+
+// Central angle (0 .. pi) of the arc from P to a hit `chord` away, with `sumlen` the
+// length of (P - c) + (p - c): 2 asin(chord / 2R) up to x = 0.7, and pi - 2 asin(sumlen /
+// 2R) beyond, where the first form is ill-conditioned in FP32.
+__device__ __forceinline__ float central_angle(float chord, float sumlen, float inv2r)
+{
+    const float x = chord * inv2r;
+    const bool far = !(x <= 0.7f);
+    const float arg = far ? fminf(sumlen * inv2r, 1.0f) : x;
+    const float h = 2.0f * asinf(arg);
+    return far ? 3.14159265f - h : h;
+}
+
+// Accurate longitudinal part: signed path lengths from P and the least-squares line.
+// The path length of the first hit, s_1 = +-R * angle(P - c, p1 - c), is computed
+// directly (its error shifts all s alike, which the slope does not see); the others as
+// s_1 + R psi_k, psi_k the signed angle from p1 to p_k about the centre taken from the
+// exact hit difference e = p_k - p1: 2 asin(|e| / 2R) for short chords, and
+// atan2(|b x e|, b.(b + e)), b = p1 - c, for long ones; its sign is that of b x e, and a
+// turn 2 pi R is added or removed as a crude estimate of s_k requires.  The slope stays
+// accurate when a hit with a large z residual has little lever.
+__device__ __forceinline__ int fit_longitudinal(const float4 &p1, const float4 &p2,
+                                                const float4 &p3, const Trans &t,
+                                                const FitConst &C, float &cot, float &z0)
+{
+    const float rcn = 1.0f / t.cn;
+    const float ax = -t.R * t.cx * rcn, ay = -t.R * t.cy * rcn;          // P - c
+    const float b0x = -t.cpx, b0y = -t.cpy;                              // p1 - c
+    const float dx0 = p1.x - t.px, dy0 = p1.y - t.py;
+    const float ch0 = sqrtf(fmaf(dx0, dx0, dy0 * dy0));
+    const float sx = ax + b0x, sy = ay + b0y;
+    const float th0 = central_angle(ch0, sqrtf(fmaf(sx, sx, sy * sy)), t.inv2r);
+    const float s0 = (t.sgn * det2(dx0, dy0, t.cx, t.cy) >= 0.0f) ? t.R * th0 : -t.R * th0;
+    const float turn = 6.2831853f * t.R;
+    const float4 *pk[3] = {&p1, &p2, &p3};
+    float dl[3];
+    dl[0] = 0.0f;
 #pragma unroll
     for (int k = 1; k < 3; ++k) {
-        const float ch = k == 1 ? cu : cv;
-        const float x = ch * inv2r;
-        float a;
-        if (x <= 0.7f) {
-            a = twor * asinf(x);
+        const float ex = k == 1 ? t.ux : t.vx, ey = k == 1 ? t.uy : t.vy;
+        const float ee = k == 1 ? t.uu : t.vv;
+        const float cr = det2(b0x, b0y, ex, ey);
+        const float xe = sqrtf(ee) * t.inv2r;
+        float psi;
+        if (xe <= 0.7f) {
+            psi = 2.0f * asinf(xe);
         } else {
-            const float cr = det2(bx[0], by[0], bx[k], by[k]);
-            const float dt = fmaf(bx[0], bx[k], by[0] * by[k]);
-            a = R * fabsf(atan2f(cr, dt));
+            const float dt = fmaf(b0x, b0x + ex, b0y * (b0y + ey));
+            psi = atan2f(fabsf(cr), dt);
         }
-        const float coarse = s[k] - s[0];
-        const float cand[4] = {a, -a, a - turn, turn - a};
-        float best = cand[0], berr = fabsf(cand[0] - coarse);
-#pragma unroll
-        for (int q = 1; q < 4; ++q) {
-            const float e = fabsf(cand[q] - coarse);
-            if (e < berr) {
-                berr = e;
-                best = cand[q];
-            }
+        const float d = (t.sgn * cr >= 0.0f) ? t.R * psi : -t.R * psi;
+        // crude s_k (good to a fraction of pi R): chord (1 + x^2/6) with its sign
+        const float dx = pk[k]->x - t.px, dy = pk[k]->y - t.py;
+        const float ch = sqrtf(fmaf(dx, dx, dy * dy));
+        const float xk = ch * t.inv2r;
+        const float mag = ch * fmaf(xk * xk, 1.0f / 6.0f, 1.0f);
+        const float crude = (t.sgn * det2(dx, dy, t.cx, t.cy) >= 0.0f) ? mag : -mag;
+        const float want = crude - s0;
+        float best = d, berr = fabsf(d - want);
+        const float dm = d - turn, dp = d + turn;
+        if (fabsf(dm - want) < berr) {
+            best = dm;
+            berr = fabsf(dm - want);
         }
-        dlt[k] = best;
+        if (fabsf(dp - want) < berr)
+            best = dp;
+        dl[k] = best;
     }
-    const float dbar = (dlt[1] + dlt[2]) * (1.0f / 3.0f);
-    const float sbar = s[0] + dbar;
+    const float dbar = (dl[1] + dl[2]) * (1.0f / 3.0f);
+    const float sbar = s0 + dbar;
     const float zbar = (p1.z + p2.z + p3.z) * (1.0f / 3.0f);
-    const float a0 = -dbar, a1 = dlt[1] - dbar, a2 = dlt[2] - dbar;
+    const float a0 = -dbar, a1 = dl[1] - dbar, a2 = dl[2] - dbar;
     const float sss = fmaf(a0, a0, fmaf(a1, a1, a2 * a2));
     const float ssz = fmaf(a0, p1.z - zbar, fmaf(a1, p2.z - zbar, a2 * (p3.z - zbar)));
     if (!(sss > 0.0f))
         return kNeedFp64;
-    const float cot = ssz / sss;
-    const float z0 = fmaf(-cot, sbar, zbar);
+    cot = ssz / sss;
+    z0 = fmaf(-cot, sbar, zbar);
     if (!in_range_f32(C, 3, cot) || !in_range_f32(C, 4, z0))
         return kReject;
-    r.cx = cx;
-    r.cy = cy;
-    r.sgn = sgn;
-    r.qopt = qopt;
-    r.d0 = d0;
+    return kPass;
+}
+
+// Everything but phi0 for points p1, p2, p3 (x, y, z in .x .y .z).
+__device__ __forceinline__ int fit_stage_b(const float4 &p1, const float4 &p2, const float4 &p3,
+                                           const FitConst &C, FitB &r)
+{
+    Trans t;
+    const int st = fit_transverse(p1, p2, p3, C, t);
+    if (st != kPass)
+        return st;
+    float cot, z0;
+    const int sl = fit_longitudinal(p1, p2, p3, t, C, cot, z0);
+    if (sl != kPass)
+        return sl;
+    r.cx = t.cx;
+    r.cy = t.cy;
+    r.sgn = t.sgn;
+    r.qopt = t.qopt;
+    r.d0 = t.d0;
     r.cot = cot;
     r.z0 = z0;
     return kPass;

@@ -500,17 +500,19 @@ __global__ void k_cand_emit(const uint32_t *cbits, const uint32_t *wprefix, int6
                             int64_t W, const int32_t *hist, FitConst C, trk_candidate *cand,
                             int32_t *fill, int64_t cand_cap, Counters *ctr)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t gw = warp0; gw < n_words; gw += nwarps) {
-        const uint32_t word = cbits[gw];
+    // a thread per bitmap word; the few set bits are expanded serially
+    for (int64_t gw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gw < n_words;
+         gw += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t word = cbits[gw];
         if (word == 0)
             continue;
-        if ((word >> lane) & 1u) {
-            const int e = (int)(gw / W);
-            const uint32_t bin = (uint32_t)((gw - (int64_t)e * W) * 32 + lane);
-            const int64_t c = (int64_t)wprefix[gw] + __popc(word & lanemask_lt());
+        const int e = (int)(gw / W);
+        int64_t c = (int64_t)wprefix[gw];
+        const uint32_t base = (uint32_t)((gw - (int64_t)e * W) * 32);
+        while (word) {
+            const int bit = __ffs(word) - 1;
+            word &= word - 1;
+            const uint32_t bin = base + (uint32_t)bit;
             if (c < cand_cap) {
                 trk_candidate r;
                 r.bin = bin;
@@ -532,6 +534,7 @@ __global__ void k_cand_emit(const uint32_t *cbits, const uint32_t *wprefix, int6
             } else {
                 atomicOr(&ctr->overflow, 1ull);
             }
+            ++c;
         }
     }
 }
@@ -573,35 +576,36 @@ __global__ void k_assign_fill(AssignArgs A)
     n_chunks = n_chunks < A.chunk_cap ? n_chunks : A.chunk_cap;
     const int T = A.geo->n_triples;
     const int F = A.args->n_events * T;
+    // Only ~1 % of the votes land in candidate bins: test the bitmap first (it needs just
+    // the chunk's event), locate the work item only for those.
     for (int64_t cid = warp0; cid < n_chunks; cid += nwarps) {
-        const int item = A.chunk_item[cid];
         const int count = A.chunk_count[cid];
-        if (item < 0 || count <= 0)
+        if (count <= 0 || lane >= count)
             continue;
-        const ItemLoc loc = locate_item(item, A.item_off, F, T, A.geo, A.lay_off, A.ti, A.tj);
-        if (lane >= count)
-            continue;
+        const int e = A.chunk_event[cid];
         const uint64_t v = A.votes[cid * kWarp + lane];
         const uint32_t bin = (uint32_t)v;
-        const uint32_t code = (uint32_t)(v >> 32);
-        const size_t wpos = (size_t)loc.e * A.W + (bin >> 5);
+        const size_t wpos = (size_t)e * A.W + (bin >> 5);
         const uint32_t word = A.cbits[wpos];
         if (!((word >> (bin & 31)) & 1u))
             continue;
         const int64_t c = (int64_t)A.wprefix[wpos] + __popc(word & ((1u << (bin & 31)) - 1u));
         if (c >= A.cand_cap)
             continue;
+        const int item = A.chunk_item[cid];
+        const ItemLoc loc = locate_item(item, A.item_off, F, T, A.geo, A.lay_off, A.ti, A.tj);
         const int slot = atomicAdd(&A.fill[c], 1);
         const int64_t pos = A.vote_off[c] + 3 * (int64_t)slot;
         if (pos + 3 > A.assign_cap) {
             atomicOr(&A.ctr->overflow, 2ull);
             continue;
         }
+        const uint32_t code = (uint32_t)(v >> 32);
         const uint32_t pair = code >> 24, kl = code & 0xffffffu;
         const int ip = loc.a_first + (int)(pair / A.tj);
         const int jp = loc.b_first + (int)(pair % A.tj);
         const int kp = loc.c_first + (int)kl;
-        const int64_t eb = A.ev_begin[loc.e];
+        const int64_t eb = A.ev_begin[e];
         A.assign[pos] = __float_as_int(A.packed[ip].w) - (int)eb;
         A.assign[pos + 1] = __float_as_int(A.packed[jp].w) - (int)eb;
         A.assign[pos + 2] = __float_as_int(A.packed[kp].w) - (int)eb;
@@ -799,7 +803,7 @@ cudaError_t launch_cand_emit(const uint32_t *cbits, const uint32_t *wprefix, int
                              trk_candidate *cand, int32_t *fill, int64_t cand_cap, Counters *ctr,
                              int n_sm, cudaStream_t s)
 {
-    int64_t grid = (n_words + 7) / 8;
+    int64_t grid = (n_words + 255) / 256;
     const int64_t cap = (int64_t)n_sm * 16;
     grid = grid < cap ? grid : cap;
     k_cand_emit<<<(unsigned)(grid > 0 ? grid : 1), 256, 0, s>>>(cbits, wprefix, n_words, W, hist,

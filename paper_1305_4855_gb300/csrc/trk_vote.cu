@@ -1,306 +1,16 @@
-// Triplet enumeration + helix fit + vote: the hot loop (paper Sec. 7 and Fig. 3: every
-// hit combination votes into the parameter space; Sec. 8: concurrent votes race, so the
-// accumulation is done with atomics).
-//
-// Persistent blocks pull work items (event, layer triple, tile of inner x middle hits)
-// from a device counter.  Each thread owns one (inner, middle) hit pair and walks the
-// outer-layer hits, staged in shared memory, through three stages:
-//   A  curvature prefilter (13 FP32 ops): a superset test of the q/pT range;
-//   B  the full FP32 fit up to (q/pT, d0, cot, z0) with early range rejections;
-//   C  phi0, the five bin indices, the histogram atomic and the vote-list record.
-// Between stages the surviving (pair, hit) items are compacted into per-warp ring
-// queues in shared memory so that B and C run with all 32 lanes busy.  Fits that the
-// FP32 path cannot resolve (near-collinear, degenerate) are recomputed in FP64.
-#include "trk_common.cuh"
+// Triplet fit kernel for explicit triplets, and dispatch of the vote kernel over its
+// occupancy levels (each level is instantiated in its own translation unit so that the
+// big kernel compiles in parallel).
+#include "trk_vote_kernel.cuh"
 
 namespace trk {
 
-
-
-struct Q1 {                       // stage-A survivor: outer hit and its code
-    float x, y, z;
-    uint32_t code;                // (pair << 24) | k in layer c
-};
-struct Q2 {                       // stage-B survivor
-    float cx, cy, sgn, qopt, d0, cot, z0;
-    uint32_t code;
-};
-
-constexpr int kRing = 64;
-
-template <int NW>
-struct WarpQueues {
-    Q1 q1[NW][kRing];
-    Q2 q2[NW][kRing];
-    uint64_t stg[NW][kRing];
-};
-
-// Per-warp queue state, identical in every lane.
-struct WarpState {
-    int h1, n1, h2, n2, hs, ns;
-    int64_t res_chunk;            // next reserved chunk index
-    int res_left;                 // reserved chunks left
-    unsigned long long n_fit, n_fp64, n_votes;
-};
-
-template <int NW>
-__device__ __forceinline__ void flush_votes(const VoteArgs &A, WarpQueues<NW> &Q, WarpState &ws,
-                                            int w, int lane, int count, int item, int event)
-{
-    if (ws.res_left == 0) {
-        long long base = 0;
-        if (lane == 0)
-            base = (long long)atomicAdd(&A.ctr->n_chunks, 4ull);
-        ws.res_chunk = __shfl_sync(kFull, base, 0);
-        ws.res_left = 4;
-    }
-    const int64_t cid = ws.res_chunk;
-    ws.res_chunk++;
-    ws.res_left--;
-    if (cid < A.chunk_cap) {
-        if (lane < count)
-            A.votes[cid * kWarp + lane] = Q.stg[w][(ws.hs + lane) & (kRing - 1)];
-        if (lane == 0) {
-            A.chunk_item[cid] = item;
-            A.chunk_count[cid] = count;
-        }
-    } else if (lane == 0) {
-        atomicOr(&A.status[event], TRK_EV_VOTE_OVERFLOW);
-    }
-    ws.hs = (ws.hs + count) & (kRing - 1);
-    ws.ns -= count;
-    ws.n_votes += count;
-}
-
-// Warp-uniform: lanes with `has` vote for `bin` with `code`.
-template <int NW>
-__device__ __forceinline__ void push_votes(const VoteArgs &A, WarpQueues<NW> &Q, WarpState &ws,
-                                           int w, int lane, bool has, uint32_t bin, uint32_t code,
-                                           int32_t *hist_e, int item, int event)
-{
-    const unsigned m = __ballot_sync(kFull, has);
-    if (has) {
-        atomicAdd(hist_e + bin, 1);
-        const int pos = (ws.hs + ws.ns + __popc(m & lanemask_lt())) & (kRing - 1);
-        Q.stg[w][pos] = (uint64_t)bin | ((uint64_t)code << 32);
-    }
-    ws.ns += __popc(m);
-    if (ws.ns >= kWarp) {
-        __syncwarp();
-        flush_votes(A, Q, ws, w, lane, kWarp, item, event);
-        __syncwarp();
-    }
-}
-
-// Stage C on up to 32 queued stage-B survivors.
-template <int NW>
-__device__ __forceinline__ void drain2(const VoteArgs &A, WarpQueues<NW> &Q, WarpState &ws, int w,
-                                       int lane, int count, int32_t *hist_e, int item, int event)
-{
-    __syncwarp();
-    bool has = false;
-    uint32_t bin = 0, code = 0;
-    if (lane < count) {
-        const Q2 e = Q.q2[w][(ws.h2 + lane) & (kRing - 1)];
-        FitB r;
-        r.cx = e.cx;
-        r.cy = e.cy;
-        r.sgn = e.sgn;
-        r.qopt = e.qopt;
-        r.d0 = e.d0;
-        r.cot = e.cot;
-        r.z0 = e.z0;
-        float phi0;
-        has = fit_stage_c(r, A.C, phi0, bin);
-        code = e.code;
-    }
-    ws.h2 = (ws.h2 + count) & (kRing - 1);
-    ws.n2 -= count;
-    __syncwarp();
-    push_votes(A, Q, ws, w, lane, has, bin, code, hist_e, item, event);
-}
-
-// Stage B on up to 32 queued stage-A survivors.
-template <int NW, int TJ>
-__device__ __forceinline__ void drain1(const VoteArgs &A, WarpQueues<NW> &Q, WarpState &ws, int w,
-                                       int lane, int count, const float4 *s_i, const float4 *s_j,
-                                       int32_t *hist_e, int item, int event)
-{
-    __syncwarp();
-    int st = kReject;
-    FitB r;
-    uint32_t code = 0;
-    float4 p1, p2, p3;
-    if (lane < count) {
-        const Q1 e = Q.q1[w][(ws.h1 + lane) & (kRing - 1)];
-        code = e.code;
-        const uint32_t pair = code >> 24;
-        p1 = s_i[pair / TJ];
-        p2 = s_j[pair % TJ];
-        p3 = make_float4(e.x, e.y, e.z, 0.0f);
-        st = fit_stage_b(p1, p2, p3, A.C, r);
-        ws.n_fit++;
-    }
-    ws.h1 = (ws.h1 + count) & (kRing - 1);
-    ws.n1 -= count;
-    __syncwarp();
-    // survivors of stage B into queue 2
-    {
-        const bool pass = (st == kPass);
-        const unsigned m = __ballot_sync(kFull, pass);
-        if (pass) {
-            const int pos = (ws.h2 + ws.n2 + __popc(m & lanemask_lt())) & (kRing - 1);
-            Q2 e;
-            e.cx = r.cx;
-            e.cy = r.cy;
-            e.sgn = r.sgn;
-            e.qopt = r.qopt;
-            e.d0 = r.d0;
-            e.cot = r.cot;
-            e.z0 = r.z0;
-            e.code = code;
-            Q.q2[w][pos] = e;
-        }
-        ws.n2 += __popc(m);
-        if (ws.n2 >= kWarp)
-            drain2(A, Q, ws, w, lane, kWarp, hist_e, item, event);
-    }
-    // FP64 recomputation of the near-collinear / degenerate ones (rare)
-    if (__any_sync(kFull, st == kNeedFp64)) {
-        bool has = false;
-        uint32_t bin = 0;
-        if (st == kNeedFp64) {
-            double par[5];
-            has = (fit_f64(p1, p2, p3, A.C, par, bin) == kFit64Accepted);
-            ws.n_fp64++;
-        }
-        push_votes(A, Q, ws, w, lane, has, bin, code, hist_e, item, event);
-    }
-}
-
-template <int TI, int TJ, int KC>
-__global__ void __launch_bounds__(TI *TJ, 2) k_vote(VoteArgs A)
-{
-    constexpr int NT = TI * TJ;
-    constexpr int NW = NT / kWarp;
-    extern __shared__ __align__(16) unsigned char smem[];
-    float4 *s_k = reinterpret_cast<float4 *>(smem);
-    float4 *s_i = s_k + KC;
-    float4 *s_j = s_i + TI;
-    WarpQueues<NW> &Q = *reinterpret_cast<WarpQueues<NW> *>(s_j + TJ);
-    __shared__ int64_t s_item;
-
-    const int tid = threadIdx.x;
-    const int w = tid >> 5, lane = tid & 31;
-    const int n_events = A.args->n_events;
-    const int T = A.geo->n_triples;
-    const int L1 = A.geo->n_layers + 1;
-    const int F = n_events * T;
-    const int64_t n_items = A.item_off[F];
-
-    WarpState ws;
-    ws.h1 = ws.n1 = ws.h2 = ws.n2 = ws.hs = ws.ns = 0;
-    ws.res_chunk = 0;
-    ws.res_left = 0;
-    ws.n_fit = ws.n_fp64 = ws.n_votes = 0;
-
-    for (;;) {
-        if (tid == 0)
-            s_item = (int64_t)atomicAdd(&A.ctr->work_next, 1ull);
-        __syncthreads();
-        const int64_t item = s_item;
-        __syncthreads();
-        if (item >= n_items)
-            break;
-        const int f = upper_index(A.item_off, F, item);
-        const int e = f / T, t = f - e * T;
-        const int la = A.geo->triples[t][0], lb = A.geo->triples[t][1], lc = A.geo->triples[t][2];
-        const int32_t *lo = A.lay_off + (size_t)e * L1;
-        const int a0 = lo[la], na = lo[la + 1] - a0;
-        const int b0 = lo[lb], nb = lo[lb + 1] - b0;
-        const int c0 = lo[lc], nc = lo[lc + 1] - c0;
-        const int64_t local = item - A.item_off[f];
-        const int ntj = (nb + TJ - 1) / TJ;
-        const int ti = (int)(local / ntj), tj = (int)(local - (int64_t)ti * ntj);
-        const int i0 = ti * TI, j0 = tj * TJ;
-        if (tid < TI)
-            s_i[tid] = (i0 + tid < na) ? __ldg(A.packed + a0 + i0 + tid) : make_float4(0, 0, 0, 0);
-        else if (tid < TI + TJ)
-            s_j[tid - TI] = (j0 + tid - TI < nb) ? __ldg(A.packed + b0 + j0 + tid - TI)
-                                                 : make_float4(0, 0, 0, 0);
-        int32_t *hist_e = A.hist + (size_t)e * A.C.nbins;
-        __syncthreads();
-
-        const int pi = tid / TJ, pj = tid - (tid / TJ) * TJ;
-        const bool valid = (i0 + pi < na) && (j0 + pj < nb);
-        const float4 p1 = s_i[pi], p2 = s_j[pj];
-        const float ux = p2.x - p1.x, uy = p2.y - p1.y;
-        const float uu = fmaf(ux, ux, uy * uy);
-        const float pre = A.C.pre_k2 * uu;
-        const uint32_t pair_code = (uint32_t)tid << 24;
-
-        for (int kc = 0; kc < nc; kc += KC) {
-            const int cnt = min(KC, nc - kc);
-            for (int x = tid; x < cnt; x += NT)
-                s_k[x] = __ldg(A.packed + c0 + kc + x);
-            __syncthreads();
-            for (int kk = 0; kk < cnt; ++kk) {
-                const float4 p3 = s_k[kk];
-                const float vx = p3.x - p1.x, vy = p3.y - p1.y;
-                const float wx = p3.x - p2.x, wy = p3.y - p2.y;
-                const float D = fmaf(ux, vy, -(uy * vx));
-                const float vv = fmaf(vx, vx, vy * vy);
-                const float ww = fmaf(wx, wx, wy * wy);
-                const bool pass = valid && (D * D <= pre * (vv * ww));
-                const unsigned m = __ballot_sync(kFull, pass);
-                if (pass) {
-                    const int pos = (ws.h1 + ws.n1 + __popc(m & lanemask_lt())) & (kRing - 1);
-                    Q1 q;
-                    q.x = p3.x;
-                    q.y = p3.y;
-                    q.z = p3.z;
-                    q.code = pair_code | (uint32_t)(kc + kk);
-                    Q.q1[w][pos] = q;
-                }
-                ws.n1 += __popc(m);
-                if (ws.n1 >= kWarp)
-                    drain1<NW, TJ>(A, Q, ws, w, lane, kWarp, s_i, s_j, hist_e, (int)item, e);
-            }
-            __syncthreads();
-        }
-        // end of the work item: drain everything (partial rounds)
-        if (ws.n1 > 0)
-            drain1<NW, TJ>(A, Q, ws, w, lane, ws.n1, s_i, s_j, hist_e, (int)item, e);
-        while (ws.n2 > 0)
-            drain2(A, Q, ws, w, lane, min(ws.n2, kWarp), hist_e, (int)item, e);
-        if (ws.ns > 0) {
-            __syncwarp();
-            flush_votes(A, Q, ws, w, lane, ws.ns, (int)item, e);
-        }
-        __syncwarp();
-    }
-    // release reserved chunks that stayed empty
-    for (int r = 0; r < ws.res_left; ++r) {
-        const int64_t cid = ws.res_chunk + r;
-        if (lane == 0 && cid < A.chunk_cap) {
-            A.chunk_item[cid] = -1;
-            A.chunk_count[cid] = 0;
-        }
-    }
-    // statistics
-    unsigned long long nf = ws.n_fit, n64 = ws.n_fp64;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        nf += __shfl_xor_sync(kFull, nf, o);
-        n64 += __shfl_xor_sync(kFull, n64, o);
-    }
-    if (lane == 0) {
-        atomicAdd(&A.ctr->n_fit, nf);
-        if (n64)
-            atomicAdd(&A.ctr->n_fp64, n64);
-        atomicAdd(&A.ctr->n_votes, ws.n_votes);
-    }
-}
+cudaError_t vote_dispatch_level2(int op, int ti, int tj, const VoteArgs *A, int grid,
+                                 cudaStream_t s, int *blocks);
+cudaError_t vote_dispatch_level3(int op, int ti, int tj, const VoteArgs *A, int grid,
+                                 cudaStream_t s, int *blocks);
+cudaError_t vote_dispatch_level4(int op, int ti, int tj, const VoteArgs *A, int grid,
+                                 cudaStream_t s, int *blocks);
 
 // One-shot fit of explicit triplets with the vote kernel's arithmetic.
 __global__ void k_fit_triplets(const trk_hit *hits, int64_t n_hits, const int32_t *ijk, int64_t n,
@@ -364,79 +74,42 @@ __global__ void k_fit_triplets(const trk_hit *hits, int64_t n_hits, const int32_
 // launchers
 // ---------------------------------------------------------------------------------------
 
-template <int TI, int TJ, int KC>
-static size_t vote_smem()
+static cudaError_t vote_dispatch(int op, int ti, int tj, int level, const VoteArgs *A, int grid,
+                                 cudaStream_t s, int *blocks)
 {
-    return sizeof(float4) * (KC + TI + TJ) + sizeof(WarpQueues<TI * TJ / kWarp>);
-}
-
-template <int TI, int TJ, int KC>
-static cudaError_t launch_vote_t(const VoteArgs &A, int grid, cudaStream_t s)
-{
-    const size_t sm = vote_smem<TI, TJ, KC>();
-    k_vote<TI, TJ, KC><<<grid, TI * TJ, sm, s>>>(A);
-    return cudaGetLastError();
-}
-
-template <int TI, int TJ, int KC>
-static cudaError_t occupancy_t(int *blocks)
-{
-    const size_t sm = vote_smem<TI, TJ, KC>();
-    cudaError_t err = cudaFuncSetAttribute(k_vote<TI, TJ, KC>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err != cudaSuccess)
-        return err;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_vote<TI, TJ, KC>, TI * TJ, sm);
-}
-
-// Supported tiles: (16,16), (8,16), (16,8), (8,8), (4,16)
-#define TRK_TILES(X) X(16, 16) X(8, 16) X(16, 8) X(8, 8) X(4, 16)
-
-template <int TI, int TJ, int KC>
-static cudaError_t prepare_t()
-{
-    return cudaFuncSetAttribute(k_vote<TI, TJ, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)vote_smem<TI, TJ, KC>());
-}
-
-cudaError_t prepare_vote_kernel(int ti, int tj)
-{
-#define X(a, b)                                                                               \
-    if (ti == a && tj == b)                                                                   \
-        return prepare_t<a, b, 2048>();
-    TRK_TILES(X)
-#undef X
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_vote(const VoteArgs &A, int ti, int tj, int grid, cudaStream_t s)
-{
-#define X(a, b)                                                                               \
-    if (ti == a && tj == b)                                                                   \
-        return launch_vote_t<a, b, 2048>(A, grid, s);
-    TRK_TILES(X)
-#undef X
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t vote_occupancy(int ti, int tj, int *blocks)
-{
-#define X(a, b)                                                                               \
-    if (ti == a && tj == b)                                                                   \
-        return occupancy_t<a, b, 2048>(blocks);
-    TRK_TILES(X)
-#undef X
-    return cudaErrorInvalidValue;
+    switch (level) {
+    case 2:
+        return vote_dispatch_level2(op, ti, tj, A, grid, s, blocks);
+    case 3:
+        return vote_dispatch_level3(op, ti, tj, A, grid, s, blocks);
+    case 4:
+        return vote_dispatch_level4(op, ti, tj, A, grid, s, blocks);
+    default:
+        return cudaErrorInvalidValue;
+    }
 }
 
 bool vote_tile_supported(int ti, int tj)
 {
-#define X(a, b)                                                                               \
-    if (ti == a && tj == b)                                                                   \
-        return true;
-    TRK_TILES(X)
-#undef X
-    return false;
+    return (ti == 16 && tj == 16) || (ti == 8 && tj == 16) || (ti == 16 && tj == 8) ||
+           (ti == 8 && tj == 8) || (ti == 4 && tj == 16);
+}
+
+bool vote_level_supported(int level) { return level >= 2 && level <= 4; }
+
+cudaError_t prepare_vote_kernel(int ti, int tj, int level)
+{
+    return vote_dispatch(0, ti, tj, level, nullptr, 0, nullptr, nullptr);
+}
+
+cudaError_t launch_vote(const VoteArgs &A, int ti, int tj, int level, int grid, cudaStream_t s)
+{
+    return vote_dispatch(1, ti, tj, level, &A, grid, s, nullptr);
+}
+
+cudaError_t vote_occupancy(int ti, int tj, int level, int *blocks)
+{
+    return vote_dispatch(2, ti, tj, level, nullptr, 0, nullptr, blocks);
 }
 
 cudaError_t launch_fit_triplets(const trk_hit *hits, int64_t n_hits, const int32_t *ijk,

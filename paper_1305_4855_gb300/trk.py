@@ -19,13 +19,16 @@ LIB_PATH = os.path.join(HERE, "_build", "libtrk.so")
 TRK_MAX_LAYERS = 64
 TRK_MAX_TRIPLES = 512
 TRK_OK, TRK_ERR_INVALID, TRK_ERR_CAPACITY, TRK_ERR_CUDA, TRK_ERR_NOMEM = 0, -1, -2, -3, -4
+TRK_PENDING = -5
 TRK_EV_BAD_HIT, TRK_EV_TOO_MANY_HITS, TRK_EV_VOTE_OVERFLOW = 1, 2, 4
 TRK_EV_CAND_OVERFLOW, TRK_EV_BAD_OFFSETS = 8, 16
 
 EXPORTED = ["trk_options_default", "trk_create", "trk_reconstruct", "trk_reconstruct_host",
             "trk_destroy", "trk_get_stats", "trk_get_histogram", "trk_histogram_size",
             "trk_get_votes", "trk_fit_triplets", "trk_profile_stages", "trk_last_error", "trk_version",
-            "trk_find_peaks_noalloc"]
+            "trk_autotune",
+            "trk_find_peaks_noalloc", "trk_server_create", "trk_server_submit", "trk_server_wait",
+            "trk_server_take", "trk_server_counts", "trk_server_destroy"]
 
 
 class trk_geometry(C.Structure):
@@ -44,7 +47,8 @@ class trk_options(C.Structure):
                 ("max_hits_per_event", C.c_int32), ("vote_capacity", C.c_int64),
                 ("cand_capacity", C.c_int64), ("assign_capacity", C.c_int64),
                 ("peak_scratch_bytes", C.c_int64), ("tile_i", C.c_int32), ("tile_j", C.c_int32),
-                ("k_chunk", C.c_int32), ("blocks_per_sm", C.c_int32), ("use_graph", C.c_int32)]
+                ("k_chunk", C.c_int32), ("blocks_per_sm", C.c_int32), ("use_graph", C.c_int32),
+                ("vote_level", C.c_int32)]
 
 
 class trk_candidate(C.Structure):
@@ -60,8 +64,19 @@ class trk_candidates(C.Structure):
                 ("h_hit_ids", C.c_void_p)]
 
 
+class trk_tuning(C.Structure):
+    _fields_ = [("tile_i", C.c_int32), ("tile_j", C.c_int32), ("vote_level", C.c_int32),
+                ("vote_ms", C.c_float)]
+
+
+class trk_served_event(C.Structure):
+    _fields_ = [("status", C.c_int32), ("rc", C.c_int32), ("latency_s", C.c_double),
+                ("batch_events", C.c_int32), ("n_candidates", C.c_int64), ("n_hit_ids", C.c_int64)]
+
+
 class trk_stats(C.Structure):
-    _fields_ = [("n_triplets", C.c_int64), ("n_fit", C.c_int64), ("n_votes", C.c_int64),
+    _fields_ = [("n_triplets", C.c_int64), ("n_fit", C.c_int64), ("n_exact", C.c_int64),
+                ("n_votes", C.c_int64),
                 ("n_fp64", C.c_int64), ("n_candidates", C.c_int64), ("n_hit_ids", C.c_int64),
                 ("n_work_items", C.c_int64), ("ms_total", C.c_double)]
 
@@ -110,6 +125,21 @@ def load_library(path: str = LIB_PATH):
     lib.trk_last_error.restype = C.c_char_p
     lib.trk_find_peaks_noalloc.argtypes = [vp, i32, C.POINTER(trk_binning), vp, vp]
     lib.trk_find_peaks_noalloc.restype = C.c_int
+    lib.trk_autotune.argtypes = [vp, vp, i64, vp, i32, i32, C.POINTER(trk_tuning), vp]
+    lib.trk_autotune.restype = C.c_int
+    lib.trk_server_create.argtypes = [C.POINTER(vp), C.POINTER(trk_geometry), C.POINTER(trk_binning),
+                                      C.POINTER(trk_options), i32]
+    lib.trk_server_create.restype = C.c_int
+    lib.trk_server_submit.argtypes = [vp, vp, i64, C.POINTER(C.c_uint64)]
+    lib.trk_server_submit.restype = C.c_int
+    lib.trk_server_wait.argtypes = [vp, C.c_uint64, C.c_double, C.POINTER(trk_served_event)]
+    lib.trk_server_wait.restype = C.c_int
+    lib.trk_server_take.argtypes = [vp, C.c_uint64, vp, i64, vp, i64]
+    lib.trk_server_take.restype = C.c_int
+    lib.trk_server_counts.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    lib.trk_server_counts.restype = C.c_int
+    lib.trk_server_destroy.argtypes = [vp]
+    lib.trk_server_destroy.restype = C.c_int
     lib.trk_version.argtypes = []
     lib.trk_version.restype = C.c_char_p
     _lib = lib
@@ -283,6 +313,16 @@ class Reconstructor:
         self.lib.trk_get_stats(self.h, C.byref(s))
         return {k: getattr(s, k) for k, _ in trk_stats._fields_}
 
+    def autotune(self, hits, offsets, reps: int = 2, stream=None) -> dict:
+        """Pick the fastest vote-kernel tile and occupancy on these events."""
+        best = trk_tuning()
+        rc = self.lib.trk_autotune(self.h, C.c_void_p(hits.data_ptr()), hits.shape[0],
+                                   C.c_void_p(offsets.data_ptr()), offsets.numel() - 1, reps,
+                                   C.byref(best), C.c_void_p(_stream_handle(stream)))
+        if rc != TRK_OK:
+            raise TrkError(rc, self.error())
+        return {k: getattr(best, k) for k, _ in trk_tuning._fields_}
+
     def stage_ms(self, stream=None) -> dict:
         """Device time of the stages of the last call (ms)."""
         ms = (C.c_float * 8)()
@@ -331,3 +371,66 @@ class Reconstructor:
         if rc != TRK_OK:
             raise TrkError(rc, self.error())
         return params[:n], bins[:n], flags[:n]
+
+
+class Server:
+    """A trk server (continuous batching over n_lanes resident handles)."""
+
+    def __init__(self, cfg: dict, lane_events: int, lane_hits: int, n_lanes: int = 2,
+                 device: int = 0, sagitta_fp64_cm: float = 1e-4, **opts):
+        self.lib = load_library()
+        self.geo = geometry_from_workload(cfg)
+        self.bin = binning_from_workload(cfg, sagitta_fp64_cm)
+        self.opt = default_options(lane_events, lane_hits, device=device, **opts)
+        s = C.c_void_p()
+        rc = self.lib.trk_server_create(C.byref(s), C.byref(self.geo), C.byref(self.bin),
+                                        C.byref(self.opt), n_lanes)
+        if rc != TRK_OK:
+            raise TrkError(rc, self.lib.trk_last_error(None).decode())
+        self.s = s
+
+    def submit(self, hits: np.ndarray) -> int:
+        """hits: host float32 (N, 4) array (x, y, z, layer id bits)."""
+        hits = np.ascontiguousarray(hits, dtype=np.float32)
+        t = C.c_uint64(0)
+        rc = self.lib.trk_server_submit(self.s, C.c_void_p(hits.ctypes.data), hits.shape[0], C.byref(t))
+        if rc != TRK_OK:
+            raise TrkError(rc, "submit failed")
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        ev = trk_served_event()
+        rc = self.lib.trk_server_wait(self.s, ticket, timeout_s, C.byref(ev))
+        if rc == TRK_PENDING:
+            return None
+        if rc != TRK_OK:
+            raise TrkError(rc, "wait failed")
+        return {k: getattr(ev, k) for k, _ in trk_served_event._fields_}
+
+    def take(self, ticket: int, info: dict):
+        """The event's candidates (CAND_DTYPE) and per-candidate hit lists (event-local)."""
+        nc, nh = int(info["n_candidates"]), int(info["n_hit_ids"])
+        cand = np.zeros(max(nc, 1), dtype=CAND_DTYPE)
+        hits = np.zeros(max(nh, 1), dtype=np.int32)
+        rc = self.lib.trk_server_take(self.s, ticket, C.c_void_p(cand.ctypes.data), nc,
+                                      C.c_void_p(hits.ctypes.data), nh)
+        if rc != TRK_OK:
+            raise TrkError(rc, "take failed")
+        cand = cand[:nc]
+        return cand, [hits[int(c["hit_off"]):int(c["hit_off"]) + int(c["n_hits"])] for c in cand]
+
+    def counts(self) -> dict:
+        v = [C.c_int64(0) for _ in range(4)]
+        self.lib.trk_server_counts(self.s, *[C.byref(x) for x in v])
+        return dict(batches=v[0].value, events=v[1].value, failed=v[2].value, queued=v[3].value)
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.trk_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -256,3 +256,32 @@ def test_fit_triplets_precision_sample(trk):
         both = acc_o & acc_g & ~ref["amb"]
         assert np.array_equal(bins[both], ref["bin"][both])
         rec.close()
+
+
+def test_autotune_keeps_results(trk):
+    cfg = ev.load_workload("barrel10_500trk")
+    cfg["events"]["n_tracks"] = 40
+    batch = ev.make_batch(cfg, seed=17)
+    rec, res0, hits = _run(trk, cfg, batch)
+    offs = torch.from_numpy(batch.offsets).cuda()
+    best = rec.autotune(hits, offs, reps=1)
+    assert (best["tile_i"], best["tile_j"]) in [(16, 16), (8, 16), (16, 8), (8, 8), (4, 16)]
+    assert best["vote_level"] in (2, 3, 4) and best["vote_ms"] > 0
+    res1 = rec.result(rec.reconstruct_device(hits, offs))
+    assert np.array_equal(res0.cand, res1.cand)
+    assert np.array_equal(res0.hit_ids, res1.hit_ids)
+    rec.close()
+
+
+@pytest.mark.parametrize("level", [2, 3, 4])
+def test_vote_levels_agree(trk, level):
+    cfg = ev.load_workload("barrel10_500trk")
+    cfg["events"]["n_tracks"] = 30
+    batch = ev.make_batch(cfg, seed=33)
+    r0, res0, _ = _run(trk, cfg, batch)
+    r1, res1, _ = _run(trk, cfg, batch, vote_level=level)
+    assert np.array_equal(r0.histogram(0).cpu().numpy(), r1.histogram(0).cpu().numpy())
+    assert np.array_equal(res0.cand, res1.cand)
+    assert np.array_equal(res0.hit_ids, res1.hit_ids)
+    r0.close()
+    r1.close()
