@@ -276,9 +276,9 @@ int trk_server_destroy(trk_server *s);
  * plug-in that is given device buffers by a host framework and may not own any.  Such a
  * caller cannot create a trk handle (trk_create allocates its pools) but may hold vote
  * histograms.  This function applies the candidate rule of trk_reconstruct to them and
- * allocates nothing: the peak filter's scratch (8 bytes per bin) is a static device array
- * of the library, 16 MiB, present on every GPU that loads the library until the process
- * exits.
+ * allocates nothing: the peak filter's scratch (up to 12 bytes per bin) is in static device
+ * arrays of the library, 24 MiB, present on every GPU that loads the library until the
+ * process exits.
  *
  * hist: DEVICE int32, n_events dense histograms of the binning's size, row-major (as
  * trk_get_histogram writes them); cand_bits: DEVICE uint32, n_events x ceil(bins / 32)
@@ -289,11 +289,12 @@ int trk_server_destroy(trk_server *s);
  * trk_last_error(NULL) gives the reason.
  *
  * The first call on a device sets that device up (looks up the static array's device
- * address with cudaGetSymbolAddress and sets kernel attributes): make that first call
- * outside any stream capture.  Every call on a device uses the same array, which keeps
- * the last call's contents (each call writes every entry it reads, so no clearing is
- * needed); calls whose work overlaps on the GPU (other streams, other threads) race on
- * it and must be serialized by the caller. */
+ * addresses with cudaGetSymbolAddress and sets kernel attributes): make that first call
+ * outside any stream capture.  Every call on a device uses the same arrays, which keep
+ * the last call's contents (each call clears what it needs cleared -- its list counter
+ * and the caller's cand_bits -- and writes every other entry before reading it); calls
+ * whose work overlaps on the GPU (other streams, other threads) race on them and must be
+ * serialized by the caller. */
 int trk_find_peaks_noalloc(const int32_t *hist, int32_t n_events, const trk_binning *binning,
                            uint32_t *cand_bits, void *stream);
 

@@ -26,9 +26,14 @@ cudaError_t launch_schedule(const CallArgs *args, const DevGeo *geo, const int32
                             const int32_t *status, int ti, int tj, int64_t *item_off,
                             Counters *ctr, cudaStream_t s);
 size_t peak_pass1_smem(const FitConst &C, int td);
-cudaError_t launch_peaks(const int32_t *hist, uint64_t *m3, const FitConst &C, int g0, int G,
-                         int td, int threshold, const int32_t *status, uint32_t *cbits,
-                         int64_t W, int n_sm, cudaStream_t s);
+cudaError_t launch_peaks(const int32_t *hist, int32_t *m3, const FitConst &C, int g0, int G,
+                         int td, int threshold, const int32_t *status,
+                         unsigned long long *ties, unsigned long long *n_ties, int64_t tie_cap,
+                         int n_sm, cudaStream_t s);
+cudaError_t launch_peak_ties(const int32_t *hist, const FitConst &C,
+                             const unsigned long long *ties, const unsigned long long *n_ties,
+                             int64_t tie_cap, uint32_t *cbits, int64_t W,
+                             unsigned long long *overflow, int n_sm, cudaStream_t s);
 cudaError_t launch_word_scan(const uint32_t *cbits, int64_t n_words, uint32_t *wprefix,
                              int64_t *bsum, unsigned long long *total, cudaStream_t s);
 cudaError_t launch_cand_emit(const uint32_t *cbits, const uint32_t *wprefix, int64_t n_words,
@@ -79,7 +84,7 @@ struct trk_ctx {
     FitConst C;
     int64_t nbins = 0, W = 0;
     int td = 0, group = 1, vote_grid = 0, max_words = 0, level = 3;
-    int64_t chunk_cap = 0, bsum_cap = 0;
+    int64_t chunk_cap = 0, bsum_cap = 0, tie_cap = 0;
 
     DevGeo *d_geo = nullptr;
     CallArgs *d_args = nullptr;
@@ -94,7 +99,8 @@ struct trk_ctx {
     int32_t *d_chunk_item = nullptr;
     int32_t *d_chunk_count = nullptr;
     int32_t *d_chunk_event = nullptr;
-    uint64_t *d_m3 = nullptr;
+    int32_t *d_m3 = nullptr;
+    unsigned long long *d_ties = nullptr;
     uint32_t *d_cbits = nullptr;
     uint32_t *d_wprefix = nullptr;
     int64_t *d_bsum = nullptr;
@@ -273,7 +279,7 @@ static void free_all(trk_ctx *h)
 {
     void *dev[] = {h->d_geo,       h->d_args,       h->d_ctr,         h->d_packed,   h->d_lay_off,
                    h->d_ev_begin,  h->d_status,     h->d_item_off,    h->d_hist,     h->d_votes,
-                   h->d_chunk_item, h->d_chunk_count, h->d_chunk_event, h->d_m3,        h->d_cbits,    h->d_wprefix,
+                   h->d_chunk_item, h->d_chunk_count, h->d_chunk_event, h->d_m3, h->d_ties,        h->d_cbits,    h->d_wprefix,
                    h->d_bsum,      h->d_cand,       h->d_fill,        h->d_vote_off, h->d_assign,
                    h->d_nhits,     h->d_hit_off,    h->d_hit_ids,     h->d_cand_off, h->d_in_hits,
                    h->d_in_offsets, h->d_chunk_pos};
@@ -368,11 +374,18 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
     int td = binning->n[2];
     while (td > 1 && peak_pass1_smem(C, td) > 48 * 1024)
         --td;
+    if (peak_pass1_smem(C, td) > 100 * 1024) {
+        delete h;
+        return fail(nullptr, TRK_ERR_INVALID, "n[3] * (n[4] + 1) too large for the filter tile");
+    }
     h->td = td;
-    int64_t g = o.peak_scratch_bytes / (h->nbins * 8);
+    int64_t g = o.peak_scratch_bytes / (h->nbins * 4);
     g = g < 1 ? 1 : (g > o.max_events ? o.max_events : g);
     h->group = (int)g;
     h->max_words = (o.max_hits_per_event + 31) / 32;
+    // bins listed for the tie test: at least the candidates; a flat region above threshold
+    // lists every bin of it
+    h->tie_cap = 2 * o.cand_capacity > ((int64_t)1 << 20) ? 2 * o.cand_capacity : ((int64_t)1 << 20);
     h->chunk_cap = (o.vote_capacity + 31) / 32;
     int64_t caps[] = {o.cand_capacity, (int64_t)o.max_events * h->W, h->chunk_cap};
     int64_t mc = 0;
@@ -419,6 +432,7 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
     ALLOC(d_chunk_count, h->chunk_cap);
     ALLOC(d_chunk_event, h->chunk_cap);
     ALLOC(d_m3, (int64_t)h->group * h->nbins);
+    ALLOC(d_ties, h->tie_cap);
     ALLOC(d_cbits, E * h->W);
     ALLOC(d_wprefix, E * h->W);
     ALLOC(d_bsum, h->bsum_cap);
@@ -505,11 +519,14 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     TRK_CUDA(h, mark(h->ev_st[0]));
     TRK_CUDA(h, launch_vote(va, o.tile_i, o.tile_j, h->level, h->vote_grid, s));
     TRK_CUDA(h, mark(h->ev_st[1]));
+    TRK_CUDA(h, cudaMemsetAsync(h->d_cbits, 0, sizeof(uint32_t) * (size_t)n_words, s));
     for (int g0 = 0; g0 < n_events; g0 += h->group) {
         const int G = (n_events - g0) < h->group ? (n_events - g0) : h->group;
         TRK_CUDA(h, launch_peaks(h->d_hist, h->d_m3, h->C, g0, G, h->td, h->bin.threshold,
-                                 h->d_status, h->d_cbits, h->W, h->n_sm, s));
+                                 h->d_status, h->d_ties, &ctr->n_ties, h->tie_cap, h->n_sm, s));
     }
+    TRK_CUDA(h, launch_peak_ties(h->d_hist, h->C, h->d_ties, &ctr->n_ties, h->tie_cap, h->d_cbits,
+                                 h->W, &ctr->overflow, h->n_sm, s));
     TRK_CUDA(h, mark(h->ev_st[2]));
     TRK_CUDA(h, launch_word_scan(h->d_cbits, n_words, h->d_wprefix, h->d_bsum, &ctr->n_cand, s));
     TRK_CUDA(h, launch_cand_emit(h->d_cbits, h->d_wprefix, n_words, h->W, h->d_hist, h->C,

@@ -68,7 +68,8 @@ struct Counters {
     unsigned long long n_hit_ids;    // assigned hit ids
     unsigned long long overflow;     // bit 0 candidate capacity, bit 1 assignment capacity
     unsigned long long n_exact;      // triplets through the exact longitudinal fit
-    unsigned long long pad[4];
+    unsigned long long n_ties;       // bins whose count reaches their box maximum
+    unsigned long long pad[3];
 };
 
 // A run of consecutive votes of one work item in the vote list.

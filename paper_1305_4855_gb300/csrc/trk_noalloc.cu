@@ -7,18 +7,20 @@
 // that receives device buffers from a host framework and may not own any).  Such a caller
 // cannot create a trk handle (trk_create allocates every pool), but it may already hold
 // dense vote histograms.  This entry point runs the same two peak kernels as
-// trk_reconstruct on them; the kernels' only scratch (the per-bin maximum of the keys over
-// (d0, cot, z0), 8 bytes per bin) lives in the static device array below, so nothing is
+// trk_reconstruct on them; the kernels' only scratch (the per-bin maximum count over
+// (d0, cot, z0), 4 bytes per bin, a list of the bins that reach their box maximum, up to
+// 8 bytes per bin, and its counter) lives in the static device arrays below, so nothing is
 // allocated: not by this file, not by the CUDA runtime on its behalf, not by torch.
 //
 // Costs and limits of that choice:
-//   * the array takes 16 MiB of device memory on every GPU that loads the library, until
+//   * the arrays take 24 MiB of device memory on every GPU that loads the library, until
 //     the process exits, whether or not this entry point is used;
 //   * a histogram may have at most TRK_NOALLOC_MAX_BINS (2^21) bins;
-//   * all calls share the one array, so two calls whose work overlaps on the GPU (on
+//   * all calls share the arrays, so two calls whose work overlaps on the GPU (on
 //     different streams, or from different host threads) race and corrupt each other's
-//     results; serialize them.  The array keeps the last call's contents; every bin a call
-//     reads is written earlier in that same call, so nothing needs clearing between calls.
+//     results; serialize them.  The arrays keep the last call's contents; each call writes
+//     every count it reads and clears the list counter (and the caller's candidate bits)
+//     itself before use.
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -27,17 +29,26 @@
 
 namespace trk {
 size_t peak_pass1_smem(const FitConst &C, int td);
-cudaError_t launch_peaks(const int32_t *hist, uint64_t *m3, const FitConst &C, int g0, int G,
-                         int td, int threshold, const int32_t *status, uint32_t *cbits,
-                         int64_t W, int n_sm, cudaStream_t s);
+cudaError_t launch_peaks(const int32_t *hist, int32_t *m3, const FitConst &C, int g0, int G,
+                         int td, int threshold, const int32_t *status,
+                         unsigned long long *ties, unsigned long long *n_ties, int64_t tie_cap,
+                         int n_sm, cudaStream_t s);
+cudaError_t launch_peak_ties(const int32_t *hist, const FitConst &C,
+                             const unsigned long long *ties, const unsigned long long *n_ties,
+                             int64_t tie_cap, uint32_t *cbits, int64_t W,
+                             unsigned long long *overflow, int n_sm, cudaStream_t s);
 cudaError_t prepare_pipeline_kernels();
 void set_global_error(const std::string &msg);
 }  // namespace trk
 
 using namespace trk;
 
-// The peak finder's scratch, shared by every call on a device.
-static __device__ __align__(256) uint64_t g_peak_scratch[TRK_NOALLOC_MAX_BINS];
+// The peak finder's scratch, shared by every call on a device: per-bin box maxima, the
+// list of bins that reach them (at most every bin), and [0] the list length, [1] a flag
+// set when it would overflow (impossible below TRK_NOALLOC_MAX_BINS bins).
+static __device__ __align__(256) int32_t g_peak_scratch[TRK_NOALLOC_MAX_BINS];
+static __device__ __align__(256) unsigned long long g_peak_ties[TRK_NOALLOC_MAX_BINS];
+static __device__ __align__(256) unsigned long long g_peak_counters[2];
 // Per-event status read by the peak kernels: always zero (never written).
 static __device__ __align__(256) int32_t g_zero_status[1];
 
@@ -47,7 +58,9 @@ constexpr int kMaxDevices = 64;
 
 struct DeviceSetup {
     bool ready = false;
-    uint64_t *scratch = nullptr;   // device address of g_peak_scratch
+    int32_t *scratch = nullptr;    // device address of g_peak_scratch
+    unsigned long long *ties = nullptr;      // g_peak_ties
+    unsigned long long *counters = nullptr;  // g_peak_counters
     int32_t *zero = nullptr;       // device address of g_zero_status
     int n_sm = 0;
 };
@@ -76,7 +89,17 @@ int setup_device(int dev, DeviceSetup **out)
         if (e != cudaSuccess)
             return noalloc_fail(TRK_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") +
                                                   cudaGetErrorString(e));
-        d.scratch = static_cast<uint64_t *>(p);
+        d.scratch = static_cast<int32_t *>(p);
+        e = cudaGetSymbolAddress(&p, g_peak_ties);
+        if (e != cudaSuccess)
+            return noalloc_fail(TRK_ERR_CUDA, std::string("cudaGetSymbolAddress(ties): ") +
+                                                  cudaGetErrorString(e));
+        d.ties = static_cast<unsigned long long *>(p);
+        e = cudaGetSymbolAddress(&p, g_peak_counters);
+        if (e != cudaSuccess)
+            return noalloc_fail(TRK_ERR_CUDA, std::string("cudaGetSymbolAddress(counters): ") +
+                                                  cudaGetErrorString(e));
+        d.counters = static_cast<unsigned long long *>(p);
         e = cudaGetSymbolAddress(&p, g_zero_status);
         if (e != cudaSuccess)
             return noalloc_fail(TRK_ERR_CUDA, std::string("cudaGetSymbolAddress(status): ") +
@@ -141,12 +164,23 @@ extern "C" int trk_find_peaks_noalloc(const int32_t *hist, int32_t n_events,
     C.periodic = binning->periodic;
     const int64_t W = ((int64_t)C.nbins + 31) / 32;
     int td = binning->n[2];
-    while (td > 1 && peak_pass1_smem(C, td) > 200 * 1024)
+    while (td > 1 && peak_pass1_smem(C, td) > 48 * 1024)
         --td;
     cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemsetAsync(cand_bits, 0, sizeof(uint32_t) * (size_t)W * n_events, s);
+    if (e != cudaSuccess)
+        return noalloc_fail(TRK_ERR_CUDA, std::string("clearing cand_bits: ") +
+                                              cudaGetErrorString(e));
     for (int ev = 0; ev < n_events; ++ev) {
-        e = launch_peaks(hist + (size_t)ev * C.nbins, d->scratch, C, 0, 1, td,
-                         binning->threshold, d->zero, cand_bits + (size_t)ev * W, W, d->n_sm, s);
+        e = cudaMemsetAsync(d->counters, 0, 2 * sizeof(unsigned long long), s);
+        if (e == cudaSuccess)
+            e = launch_peaks(hist + (size_t)ev * C.nbins, d->scratch, C, 0, 1, td,
+                             binning->threshold, d->zero, d->ties, d->counters,
+                             TRK_NOALLOC_MAX_BINS, d->n_sm, s);
+        if (e == cudaSuccess)
+            e = launch_peak_ties(hist + (size_t)ev * C.nbins, C, d->ties, d->counters,
+                                 TRK_NOALLOC_MAX_BINS, cand_bits + (size_t)ev * W, W,
+                                 d->counters + 1, d->n_sm, s);
         if (e != cudaSuccess)
             return noalloc_fail(TRK_ERR_CUDA, std::string("peak kernels: ") +
                                                   cudaGetErrorString(e));

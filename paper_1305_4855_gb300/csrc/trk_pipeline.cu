@@ -190,30 +190,23 @@ __global__ void __launch_bounds__(kSchedThreads) k_schedule(const CallArgs *args
 }
 
 // ---------------------------------------------------------------------------------------
-// a5: peaks.  Key of a bin: (count << 32) | ~bin.  A bin satisfies the rule (count >= all
-// neighbours, > the neighbours with a smaller number) iff its key is the strict maximum of
-// the keys of its 3^5 neighbourhood; the maximum over the box is separable.  Pass 1 takes
-// the maximum over (d0, cot, z0) in shared memory, pass 2 over (phi0, q/pT) and compares.
+// a5: peaks.  Bin b is a candidate iff h[b] >= T, h[b] >= h[m] for every neighbour m of its
+// 3^5 box, and h[b] > h[m] for the neighbours with a smaller bin number.  The first two
+// conditions say h[b] equals the maximum count over the box, which is separable: pass 1
+// takes it over (d0, cot, z0) in shared memory, pass 2 over (phi0, q/pT) with a sliding
+// window along phi0 and lists the bins that reach it; the tie pass then drops the listed
+// bins that have an equal neighbour with a smaller bin number and sets the candidate bits.
 // ---------------------------------------------------------------------------------------
 
-__device__ __forceinline__ uint64_t key_of(int32_t h, uint32_t lin)
-{
-    return ((uint64_t)(uint32_t)h << 32) | (uint64_t)(~lin);
-}
+__device__ __forceinline__ int max3i(int a, int b, int c) { return max(max(a, b), c); }
 
-__device__ __forceinline__ uint64_t max3(uint64_t a, uint64_t b, uint64_t c)
+// In-place maximum over {i-1, i, i+1} along a line of n counts with the given stride.
+__device__ __forceinline__ void line_max3(int32_t *p, int n, int stride)
 {
-    const uint64_t m = a > b ? a : b;
-    return m > c ? m : c;
-}
-
-// In-place max over {i-1, i, i+1} along a line of n elements with the given stride.
-__device__ __forceinline__ void line_max3(uint64_t *p, int n, int stride)
-{
-    uint64_t prev = 0, cur = p[0];
+    int prev = 0, cur = p[0];
     for (int i = 0; i < n; ++i) {
-        const uint64_t next = (i + 1 < n) ? p[(i + 1) * stride] : 0;
-        p[i * stride] = max3(prev, cur, next);
+        const int next = (i + 1 < n) ? p[(i + 1) * stride] : 0;
+        p[i * stride] = max3i(prev, cur, next);
         prev = cur;
         cur = next;
     }
@@ -221,11 +214,11 @@ __device__ __forceinline__ void line_max3(uint64_t *p, int n, int stride)
 
 constexpr int kPeakThreads = 256;
 
-__global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist, uint64_t *m3,
+__global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist, int32_t *m3,
                                                              FitConst C, int g0, int td,
                                                              const int32_t *status)
 {
-    extern __shared__ uint64_t sk[];
+    extern __shared__ int32_t sk[];
     const int n0 = C.n[0], n1 = C.n[1], n2 = C.n[2], n3 = C.n[3], n4 = C.n[4];
     const int P4 = n4 + 1;
     const int nslab = (n2 + td - 1) / td;
@@ -250,12 +243,10 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist
         const int lr = x / plane, rem = x - lr * plane;
         const int i3 = rem / n4, i4 = rem - i3 * n4;
         const int d = d_start + lr - 1;
-        uint64_t key = 0;
-        if (d >= 0 && d < n2) {
-            const uint32_t lin = base + (uint32_t)d * C.stride[2] + (uint32_t)rem;
-            key = key_of(h_e[lin], lin);
-        }
-        sk[(lr * n3 + i3) * P4 + i4] = key;
+        int v = 0;
+        if (d >= 0 && d < n2)
+            v = h_e[base + (uint32_t)d * C.stride[2] + (uint32_t)rem];
+        sk[(lr * n3 + i3) * P4 + i4] = v;
     }
     __syncthreads();
     for (int line = tid; line < (rows + 2) * n3; line += kPeakThreads)
@@ -266,67 +257,130 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist
         line_max3(sk + lr * n3 * P4 + i4, n3, P4);
     }
     __syncthreads();
-    uint64_t *out = m3 + (size_t)ge * C.nbins + base + (uint32_t)d_start * C.stride[2];
+    int32_t *out = m3 + (size_t)ge * C.nbins + base + (uint32_t)d_start * C.stride[2];
     const int rs = n3 * P4;
     for (int line = tid; line < plane; line += kPeakThreads) {
         const int i3 = line / n4, i4 = line - i3 * n4;
-        const uint64_t *p = sk + i3 * P4 + i4;
-        uint64_t prev = p[0], cur = p[rs];
+        const int32_t *q = sk + i3 * P4 + i4;
+        int prev = q[0], cur = q[rs];
         for (int r = 0; r < rows; ++r) {
-            const uint64_t next = p[(r + 2) * rs];
-            out[(size_t)r * plane + line] = max3(prev, cur, next);
+            const int next = q[(r + 2) * rs];
+            out[(size_t)r * plane + line] = max3i(prev, cur, next);
             prev = cur;
             cur = next;
         }
     }
 }
 
-__global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist, const uint64_t *m3,
+// Pass 2: thread per (event, q/pT row, inner position); walks phi0 keeping the maxima
+// over q/pT +-1 of the three phi0 rows around the current one.
+__global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist, const int32_t *m3,
                                                              FitConst C, int g0, int G,
                                                              int threshold, const int32_t *status,
-                                                             uint32_t *cbits, int64_t W)
+                                                             unsigned long long *ties,
+                                                             unsigned long long *n_ties,
+                                                             int64_t tie_cap)
+{
+    const int n0 = C.n[0], n1 = C.n[1];
+    const uint32_t inner = C.stride[1];
+    const bool per0 = (C.periodic & 1) != 0;
+    const int64_t total = (int64_t)G * n1 * inner;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t rest = (uint32_t)(t % inner);
+        const int64_t q = t / inner;
+        const int i1 = (int)(q % n1);
+        const int ge = (int)(q / n1);
+        const int e = g0 + ge;
+        if (status[e] != 0)
+            continue;
+        const int32_t *m = m3 + (size_t)ge * C.nbins + rest;
+        const int32_t *h_e = hist + (size_t)e * C.nbins;
+        auto colmax = [&](int j0) {
+            const int32_t *r = m + (size_t)j0 * C.stride[0];
+            int v = r[(size_t)i1 * inner];
+            if (i1 > 0)
+                v = max(v, r[(size_t)(i1 - 1) * inner]);
+            if (i1 + 1 < n1)
+                v = max(v, r[(size_t)(i1 + 1) * inner]);
+            return v;
+        };
+        int prev = per0 ? colmax(n0 - 1) : 0;
+        int cur = colmax(0);
+        const int first = cur;
+        for (int i0 = 0; i0 < n0; ++i0) {
+            int next;
+            if (i0 + 1 < n0)
+                next = colmax(i0 + 1);
+            else
+                next = per0 ? first : 0;
+            const uint32_t bin = (uint32_t)i0 * C.stride[0] + (uint32_t)i1 * inner + rest;
+            const int h = h_e[bin];
+            if (h >= threshold && h == max3i(prev, cur, next)) {
+                const unsigned long long slot = atomicAdd(n_ties, 1ull);
+                if ((int64_t)slot < tie_cap)
+                    ties[slot] = ((unsigned long long)(unsigned)e << 32) | bin;
+            }
+            prev = cur;
+            cur = next;
+        }
+    }
+}
+
+// Tie pass: warp per listed bin; candidate unless a neighbour with a smaller bin number
+// has the same count.
+__global__ void k_peak_ties(const int32_t *hist, FitConst C, const unsigned long long *ties,
+                            const unsigned long long *n_ties, int64_t tie_cap, uint32_t *cbits,
+                            int64_t W, unsigned long long *overflow)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int n0 = C.n[0], n1 = C.n[1];
+    int64_t n = (int64_t)*n_ties;
+    if (n > tie_cap) {
+        if (warp0 == 0 && lane == 0)
+            atomicOr(overflow, 1ull);
+        n = tie_cap;
+    }
+    const int n0 = C.n[0];
     const bool per0 = (C.periodic & 1) != 0;
-    for (int64_t gw = warp0; gw < (int64_t)G * W; gw += nwarps) {
-        const int ge = (int)(gw / W);
-        const int64_t wi = gw - (int64_t)ge * W;
-        const int e = g0 + ge;
-        bool cand = false;
-        const uint32_t bin = (uint32_t)(wi * 32 + lane);
-        if (status[e] == 0 && bin < C.nbins) {
-            const int32_t h = hist[(size_t)e * C.nbins + bin];
-            if (h >= threshold) {
-                const uint32_t i0 = bin / C.stride[0];
-                const uint32_t r0 = bin - i0 * C.stride[0];
-                const uint32_t i1 = r0 / C.stride[1];
-                const uint32_t rest = r0 - i1 * C.stride[1];
-                const uint64_t *m = m3 + (size_t)ge * C.nbins;
-                uint64_t mx = 0;
-                for (int d0 = -1; d0 <= 1; ++d0) {
-                    int j0 = (int)i0 + d0;
-                    if (j0 < 0 || j0 >= n0) {
-                        if (!per0)
-                            continue;
-                        j0 = (j0 + n0) % n0;
-                    }
-                    for (int d1 = -1; d1 <= 1; ++d1) {
-                        const int j1 = (int)i1 + d1;
-                        if (j1 < 0 || j1 >= n1)
-                            continue;
-                        const uint64_t v = m[(uint32_t)j0 * C.stride[0] + (uint32_t)j1 * C.stride[1] + rest];
-                        mx = v > mx ? v : mx;
-                    }
-                }
-                cand = (mx == key_of(h, bin));
-            }
+    for (int64_t i = warp0; i < n; i += nwarps) {
+        const unsigned long long key = ties[i];
+        const int e = (int)(key >> 32);
+        const uint32_t bin = (uint32_t)key;
+        const int32_t *h_e = hist + (size_t)e * C.nbins;
+        const int h = h_e[bin];
+        int idx[5];
+        uint32_t rem = bin;
+        for (int k = 0; k < 5; ++k) {
+            idx[k] = (int)(rem / C.stride[k]);
+            rem -= (uint32_t)idx[k] * C.stride[k];
         }
-        const unsigned word = __ballot_sync(kFull, cand);
-        if (lane == 0)
-            cbits[(size_t)e * W + wi] = word;
+        bool beaten = false;
+        for (int o = lane; o < 243; o += 32) {
+            int off = o;
+            uint32_t nb = 0;
+            bool ok = true;
+#pragma unroll
+            for (int k = 4; k >= 0; --k) {
+                const int dk = off % 3 - 1;
+                off /= 3;
+                int j = idx[k] + dk;
+                if (j < 0 || j >= C.n[k]) {
+                    if (k == 0 && per0)
+                        j = (j + n0) % n0;
+                    else
+                        ok = false;
+                }
+                nb += (uint32_t)j * C.stride[k];
+            }
+            const uint32_t nbin = nb;
+            if (ok && nbin < bin && h_e[nbin] == h)
+                beaten = true;
+        }
+        beaten = __any_sync(kFull, beaten);
+        if (!beaten && lane == 0)
+            atomicOr(&cbits[(size_t)e * W + (bin >> 5)], 1u << (bin & 31));
     }
 }
 
@@ -569,46 +623,64 @@ __device__ __forceinline__ ItemLoc locate_item(int64_t item, const int64_t *item
 
 __global__ void k_assign_fill(AssignArgs A)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t n_chunks = (int64_t)A.ctr->n_chunks;
     n_chunks = n_chunks < A.chunk_cap ? n_chunks : A.chunk_cap;
+    const int64_t n_slots = n_chunks * kWarp;
     const int T = A.geo->n_triples;
     const int F = A.args->n_events * T;
-    // Only ~1 % of the votes land in candidate bins: test the bitmap first (it needs just
-    // the chunk's event), locate the work item only for those.
-    for (int64_t cid = warp0; cid < n_chunks; cid += nwarps) {
-        const int count = A.chunk_count[cid];
-        if (count <= 0 || lane >= count)
-            continue;
-        const int e = A.chunk_event[cid];
-        const uint64_t v = A.votes[cid * kWarp + lane];
-        const uint32_t bin = (uint32_t)v;
-        const size_t wpos = (size_t)e * A.W + (bin >> 5);
-        const uint32_t word = A.cbits[wpos];
-        if (!((word >> (bin & 31)) & 1u))
-            continue;
-        const int64_t c = (int64_t)A.wprefix[wpos] + __popc(word & ((1u << (bin & 31)) - 1u));
-        if (c >= A.cand_cap)
-            continue;
-        const int item = A.chunk_item[cid];
-        const ItemLoc loc = locate_item(item, A.item_off, F, T, A.geo, A.lay_off, A.ti, A.tj);
-        const int slot = atomicAdd(&A.fill[c], 1);
-        const int64_t pos = A.vote_off[c] + 3 * (int64_t)slot;
-        if (pos + 3 > A.assign_cap) {
-            atomicOr(&A.ctr->overflow, 2ull);
-            continue;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // Only ~1 % of the votes land in candidate bins: each thread tests four independent
+    // vote slots against the candidate bitmap (loads in flight together) and locates the
+    // work item only for the rare candidate votes.
+    for (int64_t s0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s0 < n_slots;
+         s0 += 4 * stride) {
+        int64_t slot[4];
+        int cnt[4];
+        uint64_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            slot[u] = s0 + u * stride;
+            cnt[u] = slot[u] < n_slots ? A.chunk_count[slot[u] >> 5] : 0;
         }
-        const uint32_t code = (uint32_t)(v >> 32);
-        const uint32_t pair = code >> 24, kl = code & 0xffffffu;
-        const int ip = loc.a_first + (int)(pair / A.tj);
-        const int jp = loc.b_first + (int)(pair % A.tj);
-        const int kp = loc.c_first + (int)kl;
-        const int64_t eb = A.ev_begin[e];
-        A.assign[pos] = __float_as_int(A.packed[ip].w) - (int)eb;
-        A.assign[pos + 1] = __float_as_int(A.packed[jp].w) - (int)eb;
-        A.assign[pos + 2] = __float_as_int(A.packed[kp].w) - (int)eb;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            v[u] = ((int)(slot[u] & 31) < cnt[u]) ? A.votes[slot[u]] : 0ull;
+        int ev[4];
+        uint32_t word[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            ev[u] = ((int)(slot[u] & 31) < cnt[u]) ? A.chunk_event[slot[u] >> 5] : -1;
+            word[u] = ev[u] >= 0 ? A.cbits[(size_t)ev[u] * A.W + ((uint32_t)v[u] >> 5)] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t bin = (uint32_t)v[u];
+            if (ev[u] < 0 || !((word[u] >> (bin & 31)) & 1u))
+                continue;
+            const int e = ev[u];
+            const size_t wpos = (size_t)e * A.W + (bin >> 5);
+            const int64_t c =
+                (int64_t)A.wprefix[wpos] + __popc(word[u] & ((1u << (bin & 31)) - 1u));
+            if (c >= A.cand_cap)
+                continue;
+            const int item = A.chunk_item[slot[u] >> 5];
+            const ItemLoc loc = locate_item(item, A.item_off, F, T, A.geo, A.lay_off, A.ti, A.tj);
+            const int fslot = atomicAdd(&A.fill[c], 1);
+            const int64_t pos = A.vote_off[c] + 3 * (int64_t)fslot;
+            if (pos + 3 > A.assign_cap) {
+                atomicOr(&A.ctr->overflow, 2ull);
+                continue;
+            }
+            const uint32_t code = (uint32_t)(v[u] >> 32);
+            const uint32_t pair = code >> 24, kl = code & 0xffffffu;
+            const int ip = loc.a_first + (int)(pair / A.tj);
+            const int jp = loc.b_first + (int)(pair % A.tj);
+            const int kp = loc.c_first + (int)kl;
+            const int64_t eb = A.ev_begin[e];
+            A.assign[pos] = __float_as_int(A.packed[ip].w) - (int)eb;
+            A.assign[pos + 1] = __float_as_int(A.packed[jp].w) - (int)eb;
+            A.assign[pos + 2] = __float_as_int(A.packed[kp].w) - (int)eb;
+        }
     }
 }
 
@@ -746,7 +818,7 @@ __global__ void k_decode_votes(AssignArgs A, const int64_t *chunk_pos, int64_t n
 cudaError_t prepare_pipeline_kernels()
 {
     cudaError_t e = cudaFuncSetAttribute(k_peak_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
+                                         100 * 1024);
     if (e != cudaSuccess)
         return e;
     return cudaFuncSetAttribute(k_cand_hits, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -772,23 +844,36 @@ cudaError_t launch_schedule(const CallArgs *args, const DevGeo *geo, const int32
 
 size_t peak_pass1_smem(const FitConst &C, int td)
 {
-    return sizeof(uint64_t) * (size_t)(td + 2) * C.n[3] * (C.n[4] + 1);
+    return sizeof(int32_t) * (size_t)(td + 2) * C.n[3] * (C.n[4] + 1);
 }
 
-cudaError_t launch_peaks(const int32_t *hist, uint64_t *m3, const FitConst &C, int g0, int G,
-                         int td, int threshold, const int32_t *status, uint32_t *cbits,
-                         int64_t W, int n_sm, cudaStream_t s)
+// Peak passes 1 and 2 for events [g0, g0 + G): lists the bins whose count reaches the
+// box maximum (and the threshold).
+cudaError_t launch_peaks(const int32_t *hist, int32_t *m3, const FitConst &C, int g0, int G,
+                         int td, int threshold, const int32_t *status,
+                         unsigned long long *ties, unsigned long long *n_ties, int64_t tie_cap,
+                         int n_sm, cudaStream_t s)
 {
     const size_t sm = peak_pass1_smem(C, td);
     const int nslab = (C.n[2] + td - 1) / td;
     const int64_t grid1 = (int64_t)G * C.n[0] * C.n[1] * nslab;
     k_peak_pass1<<<(unsigned)grid1, kPeakThreads, sm, s>>>(hist, m3, C, g0, td, status);
-    const int64_t words = (int64_t)G * W;
-    int64_t grid2 = (words + (kPeakThreads / 32) - 1) / (kPeakThreads / 32);
-    const int64_t cap2 = (int64_t)n_sm * 16;
+    const int64_t threads = (int64_t)G * C.n[1] * C.stride[1];
+    int64_t grid2 = (threads + kPeakThreads - 1) / kPeakThreads;
+    const int64_t cap2 = (int64_t)n_sm * 32;
     grid2 = grid2 < cap2 ? grid2 : cap2;
     k_peak_pass2<<<(unsigned)(grid2 > 0 ? grid2 : 1), kPeakThreads, 0, s>>>(
-        hist, m3, C, g0, G, threshold, status, cbits, W);
+        hist, m3, C, g0, G, threshold, status, ties, n_ties, tie_cap);
+    return cudaGetLastError();
+}
+
+// The tie pass over the listed bins; sets the candidate bits (cbits must be zeroed).
+cudaError_t launch_peak_ties(const int32_t *hist, const FitConst &C,
+                             const unsigned long long *ties, const unsigned long long *n_ties,
+                             int64_t tie_cap, uint32_t *cbits, int64_t W,
+                             unsigned long long *overflow, int n_sm, cudaStream_t s)
+{
+    k_peak_ties<<<n_sm * 8, 256, 0, s>>>(hist, C, ties, n_ties, tie_cap, cbits, W, overflow);
     return cudaGetLastError();
 }
 
@@ -820,7 +905,7 @@ cudaError_t launch_vote_offsets(const trk_candidate *cand, const unsigned long l
 
 cudaError_t launch_assign(const AssignArgs &A, int n_sm, cudaStream_t s)
 {
-    k_assign_fill<<<n_sm * 16, 256, 0, s>>>(A);
+    k_assign_fill<<<n_sm * 8, 512, 0, s>>>(A);
     return cudaGetLastError();
 }
 
