@@ -32,7 +32,7 @@ cudaError_t launch_peaks(const int32_t *hist, int32_t *m3, const FitConst &C, in
                          int n_sm, cudaStream_t s);
 cudaError_t launch_peak_ties(const int32_t *hist, const FitConst &C,
                              const unsigned long long *ties, const unsigned long long *n_ties,
-                             int64_t tie_cap, uint32_t *cbits, int64_t W,
+                             int64_t tie_cap, uint32_t *cbits, int64_t W, uint32_t *filter,
                              unsigned long long *overflow, int n_sm, cudaStream_t s);
 cudaError_t launch_word_scan(const uint32_t *cbits, int64_t n_words, uint32_t *wprefix,
                              int64_t *bsum, unsigned long long *total, cudaStream_t s);
@@ -99,9 +99,11 @@ struct trk_ctx {
     int32_t *d_chunk_item = nullptr;
     int32_t *d_chunk_count = nullptr;
     int32_t *d_chunk_event = nullptr;
+    int4 *d_chunk_loc = nullptr;
     int32_t *d_m3 = nullptr;
     unsigned long long *d_ties = nullptr;
     uint32_t *d_cbits = nullptr;
+    uint32_t *d_filter = nullptr;        // candidate filter (kFilterWords)
     uint32_t *d_wprefix = nullptr;
     int64_t *d_bsum = nullptr;
     trk_candidate *d_cand = nullptr;
@@ -279,7 +281,9 @@ static void free_all(trk_ctx *h)
 {
     void *dev[] = {h->d_geo,       h->d_args,       h->d_ctr,         h->d_packed,   h->d_lay_off,
                    h->d_ev_begin,  h->d_status,     h->d_item_off,    h->d_hist,     h->d_votes,
-                   h->d_chunk_item, h->d_chunk_count, h->d_chunk_event, h->d_m3, h->d_ties,        h->d_cbits,    h->d_wprefix,
+                   h->d_chunk_item, h->d_chunk_count, h->d_chunk_event, h->d_chunk_loc,
+                   h->d_m3,        h->d_ties,
+                   h->d_cbits,     h->d_filter,     h->d_wprefix,
                    h->d_bsum,      h->d_cand,       h->d_fill,        h->d_vote_off, h->d_assign,
                    h->d_nhits,     h->d_hit_off,    h->d_hit_ids,     h->d_cand_off, h->d_in_hits,
                    h->d_in_offsets, h->d_chunk_pos};
@@ -431,9 +435,11 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
     ALLOC(d_chunk_item, h->chunk_cap);
     ALLOC(d_chunk_count, h->chunk_cap);
     ALLOC(d_chunk_event, h->chunk_cap);
+    ALLOC(d_chunk_loc, h->chunk_cap);
     ALLOC(d_m3, (int64_t)h->group * h->nbins);
     ALLOC(d_ties, h->tie_cap);
     ALLOC(d_cbits, E * h->W);
+    ALLOC(d_filter, (int64_t)kFilterWords);
     ALLOC(d_wprefix, E * h->W);
     ALLOC(d_bsum, h->bsum_cap);
     ALLOC(d_cand, o.cand_capacity);
@@ -513,6 +519,7 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     va.chunk_item = h->d_chunk_item;
     va.chunk_count = h->d_chunk_count;
     va.chunk_event = h->d_chunk_event;
+    va.chunk_loc = h->d_chunk_loc;
     va.chunk_cap = h->chunk_cap;
     va.ctr = ctr;
     va.C = h->C;
@@ -520,13 +527,14 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     TRK_CUDA(h, launch_vote(va, o.tile_i, o.tile_j, h->level, h->vote_grid, s));
     TRK_CUDA(h, mark(h->ev_st[1]));
     TRK_CUDA(h, cudaMemsetAsync(h->d_cbits, 0, sizeof(uint32_t) * (size_t)n_words, s));
+    TRK_CUDA(h, cudaMemsetAsync(h->d_filter, 0, sizeof(uint32_t) * kFilterWords, s));
     for (int g0 = 0; g0 < n_events; g0 += h->group) {
         const int G = (n_events - g0) < h->group ? (n_events - g0) : h->group;
         TRK_CUDA(h, launch_peaks(h->d_hist, h->d_m3, h->C, g0, G, h->td, h->bin.threshold,
                                  h->d_status, h->d_ties, &ctr->n_ties, h->tie_cap, h->n_sm, s));
     }
     TRK_CUDA(h, launch_peak_ties(h->d_hist, h->C, h->d_ties, &ctr->n_ties, h->tie_cap, h->d_cbits,
-                                 h->W, &ctr->overflow, h->n_sm, s));
+                                 h->W, h->d_filter, &ctr->overflow, h->n_sm, s));
     TRK_CUDA(h, mark(h->ev_st[2]));
     TRK_CUDA(h, launch_word_scan(h->d_cbits, n_words, h->d_wprefix, h->d_bsum, &ctr->n_cand, s));
     TRK_CUDA(h, launch_cand_emit(h->d_cbits, h->d_wprefix, n_words, h->W, h->d_hist, h->C,
@@ -539,6 +547,7 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     aa.chunk_item = h->d_chunk_item;
     aa.chunk_count = h->d_chunk_count;
     aa.chunk_event = h->d_chunk_event;
+    aa.chunk_loc = h->d_chunk_loc;
     aa.chunk_cap = h->chunk_cap;
     aa.item_off = h->d_item_off;
     aa.geo = h->d_geo;
@@ -547,6 +556,7 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     aa.packed = h->d_packed;
     aa.ev_begin = h->d_ev_begin;
     aa.cbits = h->d_cbits;
+    aa.filter = h->d_filter;
     aa.wprefix = h->d_wprefix;
     aa.W = h->W;
     aa.vote_off = h->d_vote_off;

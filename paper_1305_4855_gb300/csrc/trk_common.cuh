@@ -79,11 +79,16 @@ struct VoteChunk {
     int64_t offset;
 };
 
-// vote record: low 32 bits the bin, high 32 bits (pair in tile << 24) | k in layer c
-__host__ __device__ inline uint64_t make_vote(uint32_t bin, uint32_t pair, uint32_t k)
+// Vote record: low 32 bits the bin; high 32 bits the code (i << 28) | (j << 24) | k, with
+// i and j the inner and middle hit within the work item's tile (tiles are at most 16 x 16)
+// and k the outer hit within its layer (< 2^24).
+__host__ __device__ inline uint32_t vote_code(uint32_t i, uint32_t j, uint32_t k)
 {
-    return (uint64_t)bin | ((uint64_t)((pair << 24) | (k & 0xffffffu)) << 32);
+    return (i << 28) | (j << 24) | (k & 0xffffffu);
 }
+__host__ __device__ inline uint32_t code_i(uint32_t code) { return code >> 28; }
+__host__ __device__ inline uint32_t code_j(uint32_t code) { return (code >> 24) & 15u; }
+__host__ __device__ inline uint32_t code_k(uint32_t code) { return code & 0xffffffu; }
 
 // Arguments of the vote kernel.
 struct VoteArgs {
@@ -98,17 +103,34 @@ struct VoteArgs {
     int32_t *chunk_item;         // [chunk_cap] item of each 32-slot chunk (-1: empty)
     int32_t *chunk_count;        // [chunk_cap]
     int32_t *chunk_event;        // [chunk_cap] event of the chunk's item
+    int4 *chunk_loc;             // [chunk_cap] packed index of the tile's first inner, middle
+                                 // and outer-layer hit, and the item
     int64_t chunk_cap;
     Counters *ctr;
     FitConst C;
 };
 
 // Arguments of the assignment kernels.
+// Candidate filter: a one-hash Bloom filter of the candidate (event, bin) keys, sized to
+// sit in one block's shared memory, that lets the assignment skip the random lookup in the
+// candidate bitmap for most votes.  A set bit may be a false positive; a candidate's bit
+// is always set, so the filter never drops a candidate vote.
+constexpr uint32_t kFilterBits = 192u * 1024u * 8u;
+constexpr uint32_t kFilterWords = kFilterBits / 32u;
+
+__device__ __forceinline__ uint32_t cand_filter_bit(int event, uint32_t bin)
+{
+    // multiplicative (Fibonacci) hashing of the key; the high product bits pick the bit
+    const uint32_t key = bin ^ ((uint32_t)event * 0x9E3779B9u);
+    return __umulhi(key * 2654435761u, kFilterBits);
+}
+
 struct AssignArgs {
     const uint64_t *votes;
     const int32_t *chunk_item;
     const int32_t *chunk_count;
     const int32_t *chunk_event;
+    const int4 *chunk_loc;
     int64_t chunk_cap;
     const int64_t *item_off;
     const DevGeo *geo;
@@ -117,6 +139,7 @@ struct AssignArgs {
     const float4 *packed;
     const int64_t *ev_begin;
     const uint32_t *cbits;
+    const uint32_t *filter;      // kFilterWords words
     const uint32_t *wprefix;
     int64_t W;
     const int64_t *vote_off;
@@ -245,6 +268,61 @@ __device__ __forceinline__ float asin_over_x_series(float x2)
     return fmaf(x2, fmaf(x2, fmaf(x2, 5.0f / 112.0f, 3.0f / 40.0f), 1.0f / 6.0f), 1.0f);
 }
 
+// Range test widened by 1e-4 of the range width and of |p|: for the pre-tests below,
+// whose values carry a few 1e-7 of relative error.
+__device__ __forceinline__ bool in_range_loose(const FitConst &C, int k, float p)
+{
+    const float m = 1e-4f * (C.hi[k] - C.lo[k] + fabsf(p));
+    return p >= C.lo[k] - m && p < C.hi[k] + m;
+}
+
+// The transverse fit of fit_transverse evaluated for the conservative pre-test: the same
+// formulas with the MUFU square root and reciprocal (a few 1e-7 relative error per
+// operation instead of IEEE rounding) and widened q/pT and d0 range tests, so it passes
+// every triplet that fit_transverse passes.  The FP64 trigger is computed exactly as there.
+// The perigee it returns is within |P| * 1e-6 of the exact one (P = c * dist / |c| with
+// |P| = dist), far inside the margins of z_may_accept.
+__device__ __forceinline__ int fit_transverse_bound(const float4 &p1, const float4 &p2,
+                                                    const float4 &p3, const FitConst &C, Trans &t)
+{
+    t.ux = p2.x - p1.x;
+    t.uy = p2.y - p1.y;
+    t.vx = p3.x - p1.x;
+    t.vy = p3.y - p1.y;
+    const float wx = p3.x - p2.x, wy = p3.y - p2.y;
+    const float D = det2(t.ux, t.uy, t.vx, t.vy);
+    t.uu = fmaf(t.ux, t.ux, t.uy * t.uy);
+    t.vv = fmaf(t.vx, t.vx, t.vy * t.vy);
+    const float ww = fmaf(wx, wx, wy * wy);
+    if (D * D <= C.sag2 * t.vv)
+        return kNeedFp64;
+    const float sq = approx_sqrt(t.uu * t.vv * ww);
+    const float rq = approx_rcp(sq);
+    t.qopt = (-2.0f * D) * rq * C.inv_kB;
+    if (!in_range_loose(C, 1, t.qopt))
+        return kReject;
+    const float inv2d = 0.5f * approx_rcp(D);
+    t.cpx = det2(t.vy, t.uy, t.vv, t.uu) * inv2d;
+    t.cpy = det2(t.ux, t.vx, t.uu, t.vv) * inv2d;
+    t.cx = p1.x + t.cpx;
+    t.cy = p1.y + t.cpy;
+    t.R = sq * fabsf(inv2d);
+    t.inv2r = fabsf(D) * rq;
+    t.cn = approx_sqrt(fmaf(t.cx, t.cx, t.cy * t.cy));
+    const float power = fmaf(p1.x, p1.x, p1.y * p1.y) + 2.0f * fmaf(p1.x, t.cpx, p1.y * t.cpy);
+    const float dist = power * approx_rcp(t.cn + t.R);
+    t.sgn = D > 0.0f ? 1.0f : -1.0f;
+    t.d0 = t.sgn * dist;
+    if (!in_range_loose(C, 2, t.d0))
+        return kReject;
+    if (!(t.cn > 0.0f) || !(t.R < 3.0e37f))
+        return kNeedFp64;
+    const float f = dist * approx_rcp(t.cn);
+    t.px = t.cx * f;
+    t.py = t.cy * f;
+    return kPass;
+}
+
 // Conservative longitudinal test without transcendentals: may the triplet's (cot, z0) be
 // in range?  Each |s_k| is replaced by a truncated arcsine series -- chord / 2R = x <= 0.7:
 // chord (series of x); beyond, the complementary form R (pi - 2 y series(y)) with
@@ -260,23 +338,22 @@ __device__ __forceinline__ bool z_may_accept(const float4 &p1, const float4 &p2,
     const float bxs[3] = {-t.cpx, t.ux - t.cpx, t.vx - t.cpx};
     const float bys[3] = {-t.cpy, t.uy - t.cpy, t.vy - t.cpy};
     float sh[3], E[3];
+    const float twoR = 2.0f * t.R;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float dx = pk[k]->x - t.px, dy = pk[k]->y - t.py;
         const float ch = approx_sqrt(fmaf(dx, dx, dy * dy));
         const float x = ch * t.inv2r;
-        float mag, e;
-        if (x <= 0.7f) {
-            const float x2 = x * x, x4 = x2 * x2;
-            mag = ch * asin_over_x_series(x2);
-            e = ch * (0.075f * x4 * x4);
-        } else {
-            const float sx = ax + bxs[k], sy = ay + bys[k];
-            const float y = fminf(approx_sqrt(fmaf(sx, sx, sy * sy)) * t.inv2r, 1.0f);
-            const float y2 = y * y, y4 = y2 * y2;
-            mag = t.R * fmaf(-2.0f * y, asin_over_x_series(y2), 3.14159265f);
-            e = 2.0f * t.R * y * (0.075f * y4 * y4);
-        }
+        // both forms share 2R a series(a^2) with a = x (near) or y (far), and the same
+        // truncation bound 2R a 0.075 a^8; evaluated without a branch (lanes differ)
+        const float sx = ax + bxs[k], sy = ay + bys[k];
+        const float y = fminf(approx_sqrt(fmaf(sx, sx, sy * sy)) * t.inv2r, 1.0f);
+        const bool far = !(x <= 0.7f);
+        const float a = far ? y : x;
+        const float a2 = a * a, a4 = a2 * a2;
+        const float arc = twoR * a * asin_over_x_series(a2);
+        const float mag = far ? fmaf(t.R, 3.14159265f, -arc) : arc;
+        float e = twoR * a * (0.075f * a4 * a4);
         e += fmaf(4e-6f, mag, 1e-6f * t.R);
         const float pr = det2(dx, dy, t.cx, t.cy);
         if (fabsf(pr) <= 1e-3f * ch * t.cn)
@@ -336,9 +413,10 @@ __device__ __forceinline__ float central_angle(float chord, float sumlen, float 
 // directly (its error shifts all s alike, which the slope does not see); the others as
 // s_1 + R psi_k, psi_k the signed angle from p1 to p_k about the centre taken from the
 // exact hit difference e = p_k - p1: 2 asin(|e| / 2R) for short chords, and
-// atan2(|b x e|, b.(b + e)), b = p1 - c, for long ones; its sign is that of b x e, and a
-// turn 2 pi R is added or removed as a crude estimate of s_k requires.  The slope stays
-// accurate when a hit with a large z residual has little lever.
+// pi - 2 asin(|2b + e| / 2R), b = p1 - c, for long ones (the same central_angle as for
+// s_1, one arcsine and no branch); its sign is that of b x e, and a turn 2 pi R is added
+// or removed as a crude estimate of s_k requires.  The slope stays accurate when a hit
+// with a large z residual has little lever.
 __device__ __forceinline__ int fit_longitudinal(const float4 &p1, const float4 &p2,
                                                 const float4 &p3, const Trans &t,
                                                 const FitConst &C, float &cot, float &z0)
@@ -360,14 +438,9 @@ __device__ __forceinline__ int fit_longitudinal(const float4 &p1, const float4 &
         const float ex = k == 1 ? t.ux : t.vx, ey = k == 1 ? t.uy : t.vy;
         const float ee = k == 1 ? t.uu : t.vv;
         const float cr = det2(b0x, b0y, ex, ey);
-        const float xe = sqrtf(ee) * t.inv2r;
-        float psi;
-        if (xe <= 0.7f) {
-            psi = 2.0f * asinf(xe);
-        } else {
-            const float dt = fmaf(b0x, b0x + ex, b0y * (b0y + ey));
-            psi = atan2f(fabsf(cr), dt);
-        }
+        // (p1 - c) + (p_k - c) = 2 b + e for the complementary (long-chord) form
+        const float qx = fmaf(2.0f, b0x, ex), qy = fmaf(2.0f, b0y, ey);
+        const float psi = central_angle(sqrtf(ee), sqrtf(fmaf(qx, qx, qy * qy)), t.inv2r);
         const float d = (t.sgn * cr >= 0.0f) ? t.R * psi : -t.R * psi;
         // crude s_k (good to a fraction of pi R): chord (1 + x^2/6) with its sign
         const float dx = pk[k]->x - t.px, dy = pk[k]->y - t.py;

@@ -35,7 +35,7 @@ cudaError_t launch_peaks(const int32_t *hist, int32_t *m3, const FitConst &C, in
                          int n_sm, cudaStream_t s);
 cudaError_t launch_peak_ties(const int32_t *hist, const FitConst &C,
                              const unsigned long long *ties, const unsigned long long *n_ties,
-                             int64_t tie_cap, uint32_t *cbits, int64_t W,
+                             int64_t tie_cap, uint32_t *cbits, int64_t W, uint32_t *filter,
                              unsigned long long *overflow, int n_sm, cudaStream_t s);
 cudaError_t prepare_pipeline_kernels();
 void set_global_error(const std::string &msg);
@@ -180,7 +180,7 @@ extern "C" int trk_find_peaks_noalloc(const int32_t *hist, int32_t n_events,
         if (e == cudaSuccess)
             e = launch_peak_ties(hist + (size_t)ev * C.nbins, C, d->ties, d->counters,
                                  TRK_NOALLOC_MAX_BINS, cand_bits + (size_t)ev * W, W,
-                                 d->counters + 1, d->n_sm, s);
+                                 nullptr, d->counters + 1, d->n_sm, s);
         if (e != cudaSuccess)
             return noalloc_fail(TRK_ERR_CUDA, std::string("peak kernels: ") +
                                                   cudaGetErrorString(e));

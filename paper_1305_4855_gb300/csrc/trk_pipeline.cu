@@ -238,15 +238,28 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist
     const int plane = n3 * n4;
     const int32_t *h_e = hist + (size_t)e * C.nbins;
     const uint32_t base = (uint32_t)i0 * C.stride[0] + (uint32_t)i1 * C.stride[1];
+    // The slab and its two halo rows are one contiguous run of the histogram (d0 is the
+    // third-slowest axis): element x of the run is global offset (d_start - 1) * plane + x,
+    // and zero outside [0, n2 * plane).  Eight loads per thread are issued before the
+    // shared-memory stores so that the pass streams instead of waiting on each load.
     const int total = (rows + 2) * plane;
-    for (int x = tid; x < total; x += kPeakThreads) {
-        const int lr = x / plane, rem = x - lr * plane;
-        const int i3 = rem / n4, i4 = rem - i3 * n4;
-        const int d = d_start + lr - 1;
-        int v = 0;
-        if (d >= 0 && d < n2)
-            v = h_e[base + (uint32_t)d * C.stride[2] + (uint32_t)rem];
-        sk[(lr * n3 + i3) * P4 + i4] = v;
+    const int64_t g_first = (int64_t)(d_start - 1) * plane;
+    const int64_t g_end = (int64_t)n2 * plane;
+    constexpr int kL = 8;
+    for (int x0 = tid; x0 < total; x0 += kL * kPeakThreads) {
+        int v[kL];
+#pragma unroll
+        for (int u = 0; u < kL; ++u) {
+            const int x = x0 + u * kPeakThreads;
+            const int64_t g = g_first + x;
+            v[u] = (x < total && g >= 0 && g < g_end) ? __ldg(h_e + base + g) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kL; ++u) {
+            const int x = x0 + u * kPeakThreads;
+            if (x < total)
+                sk[x + x / n4] = v[u];       // row-padded: line x / n4, column x % n4
+        }
     }
     __syncthreads();
     for (int line = tid; line < (rows + 2) * n3; line += kPeakThreads)
@@ -272,8 +285,50 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist
     }
 }
 
-// Pass 2: thread per (event, q/pT row, inner position); walks phi0 keeping the maxima
-// over q/pT +-1 of the three phi0 rows around the current one.
+// Pass 2: thread per (event, q/pT row, V consecutive inner positions); walks phi0
+// keeping the maxima over q/pT +-1 of the three phi0 rows around the current one.  With
+// V = 4 (inner size a multiple of 4) every load is a 16-byte vector, so a warp reads
+// 512 contiguous bytes per row.  The bins that reach the box maximum are collected per
+// block in shared memory and appended to the global list with one atomic per block tile.
+constexpr int kTieBuf = 2048;
+
+template <int V>
+struct IntV;
+template <>
+struct IntV<1> {
+    int v[1];
+    __device__ __forceinline__ static IntV load(const int32_t *p)
+    {
+        IntV r;
+        r.v[0] = __ldg(p);
+        return r;
+    }
+};
+template <>
+struct IntV<4> {
+    int v[4];
+    __device__ __forceinline__ static IntV load(const int32_t *p)
+    {
+        const int4 q = __ldg(reinterpret_cast<const int4 *>(p));
+        IntV r;
+        r.v[0] = q.x;
+        r.v[1] = q.y;
+        r.v[2] = q.z;
+        r.v[3] = q.w;
+        return r;
+    }
+};
+
+template <int V>
+__device__ __forceinline__ IntV<V> vmax(IntV<V> a, const IntV<V> &b)
+{
+#pragma unroll
+    for (int c = 0; c < V; ++c)
+        a.v[c] = max(a.v[c], b.v[c]);
+    return a;
+}
+
+template <int V>
 __global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist, const int32_t *m3,
                                                              FitConst C, int g0, int G,
                                                              int threshold, const int32_t *status,
@@ -281,49 +336,100 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist
                                                              unsigned long long *n_ties,
                                                              int64_t tie_cap)
 {
+    __shared__ unsigned long long s_buf[kTieBuf];
+    __shared__ int s_n;
+    __shared__ unsigned long long s_base;
     const int n0 = C.n[0], n1 = C.n[1];
     const uint32_t inner = C.stride[1];
+    const uint32_t innerV = inner / V;
     const bool per0 = (C.periodic & 1) != 0;
-    const int64_t total = (int64_t)G * n1 * inner;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t rest = (uint32_t)(t % inner);
-        const int64_t q = t / inner;
+    const int64_t total = (int64_t)G * n1 * innerV;
+    if (threadIdx.x == 0)
+        s_n = 0;
+    __syncthreads();
+    // block-uniform trip count, so that every thread reaches the flush barriers
+    for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x; t0 < total;
+         t0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = t0 + threadIdx.x;
+        const uint32_t rest = (uint32_t)(t % innerV) * V;
+        const int64_t q = t / innerV;
         const int i1 = (int)(q % n1);
         const int ge = (int)(q / n1);
         const int e = g0 + ge;
-        if (status[e] != 0)
-            continue;
-        const int32_t *m = m3 + (size_t)ge * C.nbins + rest;
-        const int32_t *h_e = hist + (size_t)e * C.nbins;
-        auto colmax = [&](int j0) {
-            const int32_t *r = m + (size_t)j0 * C.stride[0];
-            int v = r[(size_t)i1 * inner];
-            if (i1 > 0)
-                v = max(v, r[(size_t)(i1 - 1) * inner]);
-            if (i1 + 1 < n1)
-                v = max(v, r[(size_t)(i1 + 1) * inner]);
-            return v;
-        };
-        int prev = per0 ? colmax(n0 - 1) : 0;
-        int cur = colmax(0);
-        const int first = cur;
-        for (int i0 = 0; i0 < n0; ++i0) {
-            int next;
-            if (i0 + 1 < n0)
-                next = colmax(i0 + 1);
-            else
-                next = per0 ? first : 0;
-            const uint32_t bin = (uint32_t)i0 * C.stride[0] + (uint32_t)i1 * inner + rest;
-            const int h = h_e[bin];
-            if (h >= threshold && h == max3i(prev, cur, next)) {
-                const unsigned long long slot = atomicAdd(n_ties, 1ull);
-                if ((int64_t)slot < tie_cap)
-                    ties[slot] = ((unsigned long long)(unsigned)e << 32) | bin;
+        if (t < total && status[e] == 0) {
+            const int32_t *m = m3 + (size_t)ge * C.nbins + rest;
+            const int32_t *h_e = hist + (size_t)e * C.nbins + rest;
+            auto colmax = [&](int j0) {
+                const int32_t *r = m + (size_t)j0 * C.stride[0];
+                IntV<V> x = IntV<V>::load(r + (size_t)i1 * inner);
+                if (i1 > 0)
+                    x = vmax(x, IntV<V>::load(r + (size_t)(i1 - 1) * inner));
+                if (i1 + 1 < n1)
+                    x = vmax(x, IntV<V>::load(r + (size_t)(i1 + 1) * inner));
+                return x;
+            };
+            // phi0 rows in groups of kR: the column maxima of rows i0+1 .. i0+kR and the
+            // counts of rows i0 .. i0+kR-1 are loaded together, then the window slides.
+            constexpr int kR = V == 1 ? 8 : 4;
+            IntV<V> zero;
+#pragma unroll
+            for (int c = 0; c < V; ++c)
+                zero.v[c] = 0;
+            IntV<V> prev = per0 ? colmax(n0 - 1) : zero;
+            IntV<V> cur = colmax(0);
+            const IntV<V> first = cur;
+            for (int c0 = 0; c0 < n0; c0 += kR) {
+                IntV<V> nx[kR], hh[kR];
+#pragma unroll
+                for (int u = 0; u < kR; ++u) {
+                    const int r = c0 + u;
+                    const int rn = r + 1;
+                    nx[u] = rn < n0 ? colmax(rn) : (rn == n0 && per0 ? first : zero);
+                    hh[u] = r < n0 ? IntV<V>::load(h_e + (size_t)r * C.stride[0] + (size_t)i1 * inner)
+                                   : zero;
+                }
+#pragma unroll
+                for (int u = 0; u < kR; ++u) {
+                    const int r = c0 + u;
+#pragma unroll
+                    for (int c = 0; c < V; ++c) {
+                        const int h = hh[u].v[c];
+                        if (r < n0 && h >= threshold && h == max3i(prev.v[c], cur.v[c], nx[u].v[c])) {
+                            const uint32_t bin = (uint32_t)r * C.stride[0] + (uint32_t)i1 * inner +
+                                                 rest + (uint32_t)c;
+                            const unsigned long long key =
+                                ((unsigned long long)(unsigned)e << 32) | bin;
+                            const int k = atomicAdd(&s_n, 1);
+                            if (k < kTieBuf) {
+                                s_buf[k] = key;
+                            } else {      // buffer full: append directly
+                                const unsigned long long slot = atomicAdd(n_ties, 1ull);
+                                if ((int64_t)slot < tie_cap)
+                                    ties[slot] = key;
+                            }
+                        }
+                    }
+                    prev = cur;
+                    cur = nx[u];
+                }
             }
-            prev = cur;
-            cur = next;
         }
+        __syncthreads();
+        const int nb = min(s_n, kTieBuf);
+        if (nb > 0) {
+            if (threadIdx.x == 0)
+                s_base = atomicAdd(n_ties, (unsigned long long)nb);
+            __syncthreads();
+            for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+                const unsigned long long slot = s_base + (unsigned long long)k;
+                if ((int64_t)slot < tie_cap)
+                    ties[slot] = s_buf[k];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            s_n = 0;
+        __syncthreads();
     }
 }
 
@@ -331,7 +437,7 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist
 // has the same count.
 __global__ void k_peak_ties(const int32_t *hist, FitConst C, const unsigned long long *ties,
                             const unsigned long long *n_ties, int64_t tie_cap, uint32_t *cbits,
-                            int64_t W, unsigned long long *overflow)
+                            int64_t W, uint32_t *filter, unsigned long long *overflow)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -379,8 +485,13 @@ __global__ void k_peak_ties(const int32_t *hist, FitConst C, const unsigned long
                 beaten = true;
         }
         beaten = __any_sync(kFull, beaten);
-        if (!beaten && lane == 0)
+        if (!beaten && lane == 0) {
             atomicOr(&cbits[(size_t)e * W + (bin >> 5)], 1u << (bin & 31));
+            if (filter) {
+                const uint32_t fb = cand_filter_bit(e, bin);
+                atomicOr(&filter[fb >> 5], 1u << (fb & 31));
+            }
+        }
     }
 }
 
@@ -621,39 +732,56 @@ __device__ __forceinline__ ItemLoc locate_item(int64_t item, const int64_t *item
 
 
 
-__global__ void k_assign_fill(AssignArgs A)
+constexpr int kAssignThreads = 1024;
+
+__global__ void __launch_bounds__(kAssignThreads, 1) k_assign_fill(AssignArgs A)
 {
+    extern __shared__ uint32_t s_filter[];
+    for (uint32_t q = threadIdx.x; q < kFilterWords / 4; q += kAssignThreads)
+        reinterpret_cast<uint4 *>(s_filter)[q] = __ldg(reinterpret_cast<const uint4 *>(A.filter) + q);
+    __syncthreads();
     int64_t n_chunks = (int64_t)A.ctr->n_chunks;
     n_chunks = n_chunks < A.chunk_cap ? n_chunks : A.chunk_cap;
     const int64_t n_slots = n_chunks * kWarp;
-    const int T = A.geo->n_triples;
-    const int F = A.args->n_events * T;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // Only ~1 % of the votes land in candidate bins: each thread tests four independent
-    // vote slots against the candidate bitmap (loads in flight together) and locates the
-    // work item only for the rare candidate votes.
+    // Only ~1 % of the votes land in candidate bins, so the kernel is a stream over the
+    // vote list.  Each thread takes kU vote slots a grid stride apart (a warp covers whole
+    // 32-slot chunks) and issues their vote, chunk count and chunk event loads together;
+    // votes are read once, with the streaming (evict-first) hint.  Slots past a chunk's
+    // count hold stale data and are discarded.  The shared-memory candidate filter then
+    // leaves the bitmap lookup (a random 32-byte L2 sector per vote) to the few votes
+    // whose filter bit is set.
+    constexpr int kU = 8;
     for (int64_t s0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s0 < n_slots;
-         s0 += 4 * stride) {
-        int64_t slot[4];
-        int cnt[4];
-        uint64_t v[4];
+         s0 += kU * stride) {
+        uint64_t v[kU];
+        int ev[kU];
+        int cnt[kU];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            slot[u] = s0 + u * stride;
-            cnt[u] = slot[u] < n_slots ? A.chunk_count[slot[u] >> 5] : 0;
+        for (int u = 0; u < kU; ++u) {
+            const int64_t slot = s0 + u * stride;
+            const bool in = slot < n_slots;
+            v[u] = in ? __ldcs(reinterpret_cast<const unsigned long long *>(A.votes) + slot) : 0ull;
+            cnt[u] = in ? __ldg(A.chunk_count + (slot >> 5)) : 0;
+            ev[u] = in ? __ldg(A.chunk_event + (slot >> 5)) : 0;
+        }
+        uint32_t word[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t slot = s0 + u * stride;
+            const uint32_t bin = (uint32_t)v[u];
+            if ((int)(slot & 31) >= cnt[u]) {
+                ev[u] = -1;
+            } else {
+                const uint32_t fb = cand_filter_bit(ev[u], bin);
+                if (!((s_filter[fb >> 5] >> (fb & 31)) & 1u))
+                    ev[u] = -1;
+            }
+            word[u] = ev[u] >= 0 ? __ldg(A.cbits + (size_t)ev[u] * A.W + (bin >> 5)) : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            v[u] = ((int)(slot[u] & 31) < cnt[u]) ? A.votes[slot[u]] : 0ull;
-        int ev[4];
-        uint32_t word[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            ev[u] = ((int)(slot[u] & 31) < cnt[u]) ? A.chunk_event[slot[u] >> 5] : -1;
-            word[u] = ev[u] >= 0 ? A.cbits[(size_t)ev[u] * A.W + ((uint32_t)v[u] >> 5)] : 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kU; ++u) {
+            const int64_t slot = s0 + u * stride;
             const uint32_t bin = (uint32_t)v[u];
             if (ev[u] < 0 || !((word[u] >> (bin & 31)) & 1u))
                 continue;
@@ -663,8 +791,7 @@ __global__ void k_assign_fill(AssignArgs A)
                 (int64_t)A.wprefix[wpos] + __popc(word[u] & ((1u << (bin & 31)) - 1u));
             if (c >= A.cand_cap)
                 continue;
-            const int item = A.chunk_item[slot[u] >> 5];
-            const ItemLoc loc = locate_item(item, A.item_off, F, T, A.geo, A.lay_off, A.ti, A.tj);
+            const int4 loc = __ldg(A.chunk_loc + (slot >> 5));
             const int fslot = atomicAdd(&A.fill[c], 1);
             const int64_t pos = A.vote_off[c] + 3 * (int64_t)fslot;
             if (pos + 3 > A.assign_cap) {
@@ -672,10 +799,9 @@ __global__ void k_assign_fill(AssignArgs A)
                 continue;
             }
             const uint32_t code = (uint32_t)(v[u] >> 32);
-            const uint32_t pair = code >> 24, kl = code & 0xffffffu;
-            const int ip = loc.a_first + (int)(pair / A.tj);
-            const int jp = loc.b_first + (int)(pair % A.tj);
-            const int kp = loc.c_first + (int)kl;
+            const int ip = loc.x + (int)code_i(code);
+            const int jp = loc.y + (int)code_j(code);
+            const int kp = loc.z + (int)code_k(code);
             const int64_t eb = A.ev_begin[e];
             A.assign[pos] = __float_as_int(A.packed[ip].w) - (int)eb;
             A.assign[pos + 1] = __float_as_int(A.packed[jp].w) - (int)eb;
@@ -801,11 +927,10 @@ __global__ void k_decode_votes(AssignArgs A, const int64_t *chunk_pos, int64_t n
             continue;
         const uint64_t v = A.votes[cid * kWarp + lane];
         const uint32_t code = (uint32_t)(v >> 32);
-        const uint32_t pair = code >> 24, kl = code & 0xffffffu;
         dst[4 * out] = loc.e;
-        dst[4 * out + 1] = __float_as_int(A.packed[loc.a_first + (int)(pair / A.tj)].w);
-        dst[4 * out + 2] = __float_as_int(A.packed[loc.b_first + (int)(pair % A.tj)].w);
-        dst[4 * out + 3] = __float_as_int(A.packed[loc.c_first + (int)kl].w);
+        dst[4 * out + 1] = __float_as_int(A.packed[loc.a_first + (int)code_i(code)].w);
+        dst[4 * out + 2] = __float_as_int(A.packed[loc.b_first + (int)code_j(code)].w);
+        dst[4 * out + 3] = __float_as_int(A.packed[loc.c_first + (int)code_k(code)].w);
         bins[out] = (uint32_t)v;
     }
 }
@@ -821,8 +946,12 @@ cudaError_t prepare_pipeline_kernels()
                                          100 * 1024);
     if (e != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_cand_hits, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                200 * 1024);
+    e = cudaFuncSetAttribute(k_cand_hits, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+    if (e != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_assign_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(uint32_t) * kFilterWords));
 }
 
 cudaError_t launch_pack(const CallArgs *args, int n_events, int L, int max_per_event,
@@ -858,22 +987,29 @@ cudaError_t launch_peaks(const int32_t *hist, int32_t *m3, const FitConst &C, in
     const int nslab = (C.n[2] + td - 1) / td;
     const int64_t grid1 = (int64_t)G * C.n[0] * C.n[1] * nslab;
     k_peak_pass1<<<(unsigned)grid1, kPeakThreads, sm, s>>>(hist, m3, C, g0, td, status);
-    const int64_t threads = (int64_t)G * C.n[1] * C.stride[1];
+    const bool vec = (C.stride[1] % 4) == 0;
+    const int64_t threads = (int64_t)G * C.n[1] * C.stride[1] / (vec ? 4 : 1);
     int64_t grid2 = (threads + kPeakThreads - 1) / kPeakThreads;
     const int64_t cap2 = (int64_t)n_sm * 32;
     grid2 = grid2 < cap2 ? grid2 : cap2;
-    k_peak_pass2<<<(unsigned)(grid2 > 0 ? grid2 : 1), kPeakThreads, 0, s>>>(
-        hist, m3, C, g0, G, threshold, status, ties, n_ties, tie_cap);
+    const unsigned g2 = (unsigned)(grid2 > 0 ? grid2 : 1);
+    if (vec)
+        k_peak_pass2<4><<<g2, kPeakThreads, 0, s>>>(hist, m3, C, g0, G, threshold, status, ties,
+                                                     n_ties, tie_cap);
+    else
+        k_peak_pass2<1><<<g2, kPeakThreads, 0, s>>>(hist, m3, C, g0, G, threshold, status, ties,
+                                                     n_ties, tie_cap);
     return cudaGetLastError();
 }
 
 // The tie pass over the listed bins; sets the candidate bits (cbits must be zeroed).
 cudaError_t launch_peak_ties(const int32_t *hist, const FitConst &C,
                              const unsigned long long *ties, const unsigned long long *n_ties,
-                             int64_t tie_cap, uint32_t *cbits, int64_t W,
+                             int64_t tie_cap, uint32_t *cbits, int64_t W, uint32_t *filter,
                              unsigned long long *overflow, int n_sm, cudaStream_t s)
 {
-    k_peak_ties<<<n_sm * 8, 256, 0, s>>>(hist, C, ties, n_ties, tie_cap, cbits, W, overflow);
+    k_peak_ties<<<n_sm * 8, 256, 0, s>>>(hist, C, ties, n_ties, tie_cap, cbits, W, filter,
+                                         overflow);
     return cudaGetLastError();
 }
 
@@ -905,7 +1041,8 @@ cudaError_t launch_vote_offsets(const trk_candidate *cand, const unsigned long l
 
 cudaError_t launch_assign(const AssignArgs &A, int n_sm, cudaStream_t s)
 {
-    k_assign_fill<<<n_sm * 8, 512, 0, s>>>(A);
+    // persistent: one block per SM (the filter takes most of the shared memory)
+    k_assign_fill<<<n_sm, kAssignThreads, sizeof(uint32_t) * kFilterWords, s>>>(A);
     return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ namespace trk {
 
 struct Q1 {                       // a (pair, outer hit) item
     float x, y, z;
-    uint32_t code;                // (pair << 24) | k in layer c
+    uint32_t code;                // vote_code(i in tile, j in tile, k in layer c)
 };
 
 constexpr int kRing = 64;
@@ -31,6 +31,7 @@ struct WarpQueues {
     Q1 q1[NW][kRing];             // survivors of the curvature prefilter
     Q1 q2[NW][kRing];             // survivors of the transverse fit and the z bound
     uint64_t stg[NW][kRing];      // votes waiting for a 32-slot chunk
+    int4 loc;                     // chunk_loc of the current work item
 };
 
 // Per-warp queue state, identical in every lane.
@@ -62,6 +63,7 @@ __device__ __forceinline__ void flush_votes(const VoteArgs &A, WarpQueues<NW> &Q
             A.chunk_item[cid] = item;
             A.chunk_count[cid] = count;
             A.chunk_event[cid] = event;
+            A.chunk_loc[cid] = Q.loc;
         }
     } else if (lane == 0) {
         atomicOr(&A.status[event], TRK_EV_VOTE_OVERFLOW);
@@ -105,9 +107,8 @@ __device__ __forceinline__ void drain2(const VoteArgs &A, WarpQueues<NW> &Q, War
     if (lane < count) {
         const Q1 e = Q.q2[w][(ws.h2 + lane) & (kRing - 1)];
         code = e.code;
-        const uint32_t pair = code >> 24;
-        p1 = s_i[pair / TJ];
-        p2 = s_j[pair % TJ];
+        p1 = s_i[code_i(code)];
+        p2 = s_j[code_j(code)];
         p3 = make_float4(e.x, e.y, e.z, 0.0f);
         FitB r;
         const int st = fit_stage_b(p1, p2, p3, A.C, r);
@@ -144,12 +145,11 @@ __device__ __forceinline__ void drain1(const VoteArgs &A, WarpQueues<NW> &Q, War
     Q1 e;
     if (lane < count) {
         e = Q.q1[w][(ws.h1 + lane) & (kRing - 1)];
-        const uint32_t pair = e.code >> 24;
-        const float4 p1 = s_i[pair / TJ];
-        const float4 p2 = s_j[pair % TJ];
+        const float4 p1 = s_i[code_i(e.code)];
+        const float4 p2 = s_j[code_j(e.code)];
         const float4 p3 = make_float4(e.x, e.y, e.z, 0.0f);
         Trans t;
-        const int st = fit_transverse(p1, p2, p3, A.C, t);
+        const int st = fit_transverse_bound(p1, p2, p3, A.C, t);
         keep = (st == kNeedFp64) || (st == kPass && z_may_accept(p1, p2, p3, t, A.C));
         ws.n_fit++;
     }
@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(TI *TJ, MINB) k_vote(VoteArgs A)
 {
     constexpr int NT = TI * TJ;
     constexpr int NW = NT / kWarp;
+    static_assert(TI <= 16 && TJ <= 16, "the vote code holds 4-bit tile positions");
     extern __shared__ __align__(16) unsigned char smem[];
     float4 *s_k = reinterpret_cast<float4 *>(smem);
     float4 *s_i = s_k + KC;
@@ -217,6 +218,8 @@ __global__ void __launch_bounds__(TI *TJ, MINB) k_vote(VoteArgs A)
             s_j[tid - TI] = (j0 + tid - TI < nb) ? __ldg(A.packed + b0 + j0 + tid - TI)
                                                  : make_float4(0, 0, 0, 0);
         int32_t *hist_e = A.hist + (size_t)e * A.C.nbins;
+        if (tid == 0)      // every warp is past the previous item's flushes (barriers above)
+            Q.loc = make_int4(a0 + i0, b0 + j0, c0, (int)item);
         __syncthreads();
 
         const int pi = tid / TJ, pj = tid - (tid / TJ) * TJ;
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(TI *TJ, MINB) k_vote(VoteArgs A)
         const float ux = p2.x - p1.x, uy = p2.y - p1.y;
         const float uu = fmaf(ux, ux, uy * uy);
         const float pre = A.C.pre_k2 * uu;
-        const uint32_t pair_code = (uint32_t)tid << 24;
+        const uint32_t pair_code = vote_code((uint32_t)pi, (uint32_t)pj, 0u);
 
         for (int kc = 0; kc < nc; kc += KC) {
             const int cnt = min(KC, nc - kc);
