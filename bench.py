@@ -55,6 +55,8 @@ def parse():
                    help="skip the batched / plain-on-batch / served measurements")
     p.add_argument("--batch-events", type=int, default=256)
     p.add_argument("--serve-seconds", type=float, default=12.0)
+    p.add_argument("--with-fit", action="store_true",
+                   help="also fit a helix to every candidate inside each timed call")
     p.add_argument("--tuning", default=None, metavar="TI,TJ,LEVEL",
                    help="fixed vote-kernel tile and occupancy level instead of the autotuner "
                         "(profiling runs: every vote launch is then the same kernel)")
@@ -245,7 +247,7 @@ def main():
         fixed = {"tile_i": ti, "tile_j": tj, "vote_level": lv}
     rec = Reconstructor(cfg, max_events=1, max_hits=batch.n_hits, device=local,
                         vote_capacity=1 << 28, cand_capacity=1 << 21, assign_capacity=1 << 25,
-                        **fixed)
+                        fit_candidates=int(args.with_fit), **fixed)
     stream = torch.cuda.Stream()
     hits = torch.from_numpy(batch.packed()).cuda()
     offs = torch.from_numpy(batch.offsets).cuda()
@@ -312,7 +314,7 @@ def main():
         "config": {"workload": args.workload, "events_per_step": 1, "hits_per_event": batch.n_hits,
                    "triplets_per_event": n_trip, "bins": rec.lib.trk_histogram_size(rec.h),
                    "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas",
-                   "tuning": tuning},
+                   "tuning": tuning, "candidate_fit": bool(args.with_fit)},
         "hit_triplets_per_s": value * n_trip,
         "stats": {k: stats[k] for k in ("n_triplets", "n_fit", "n_exact", "n_votes", "n_fp64", "n_candidates",
                                         "n_hit_ids", "n_work_items")},
@@ -328,7 +330,7 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "stage_ms": stage_ms,
         "clocks": clocks,
-        "gpu_launches": args.steps * LAUNCHES_PER_CALL,
+        "gpu_launches": args.steps * (LAUNCHES_PER_CALL + int(args.with_fit)),
     }
     rec.close()
     if not args.no_variants:
@@ -355,7 +357,8 @@ def run_variants(args, local):
     cfg = ev.load_workload(BATCH_WORKLOAD)
     batch = ev.make_batch(cfg, n_events=args.batch_events)
     n_trip = int(ev.layer_triplet_count(batch, cfg["geometry"]["triples"]).sum())
-    out = {}
+    out = {"candidate_fit": run_fit(args, local),
+           "hough2d": {w: run_hough2d(w, local) for w in ("sht_toy50", "curved_ip200")}}
     # --- batched: sub-batches of SUB events, each one trk_reconstruct (one graph launch)
     sub = 32
     per_event_max = int(np.diff(batch.offsets).max())
@@ -418,6 +421,70 @@ def run_variants(args, local):
     # --- served: open-loop Poisson arrivals (a prefix of the 1e6-event stream)
     out["served"] = run_served(args, cfg, batch, out["batched"]["events_per_s"], local)
     return out
+
+
+def run_fit(args, local):
+    """The candidate fit on the 500-track event: its stage time inside the call (CUDA
+    events around the fit kernel; the stage also holds the final offsets kernel and the
+    small count copies), and candidates fitted per second."""
+    import torch
+    from paper_1305_4855_gb300 import events as ev
+    from paper_1305_4855_gb300.trk import Reconstructor
+    cfg = ev.load_workload(WORKLOAD)
+    batch = ev.make_batch(cfg, n_events=1)
+    rec = Reconstructor(cfg, max_events=1, max_hits=batch.n_hits, device=local,
+                        vote_capacity=1 << 28, cand_capacity=1 << 21, assign_capacity=1 << 25,
+                        fit_candidates=1)
+    stream = torch.cuda.Stream()
+    hits = torch.from_numpy(batch.packed()).cuda()
+    offs = torch.from_numpy(batch.offsets).cuda()
+    fits = []
+    for i in range(8):
+        with torch.cuda.stream(stream):
+            rec.reconstruct_device(hits, offs, stream=stream)
+        st = rec.stage_ms(stream)
+        if i >= 3:
+            fits.append(st["fit"])
+    n_cand = rec.stats()["n_candidates"]
+    res = rec.result(0)
+    rec.close()
+    ms = float(np.mean(fits))
+    return {"workload": WORKLOAD, "candidates": int(n_cand), "fit_stage_ms": ms,
+            "candidates_per_s": n_cand / (ms / 1000.0),
+            "status_ok_fraction": float(np.mean(res.tracks["status"] == 0)) if n_cand else None}
+
+
+def run_hough2d(workload, local, reps=5):
+    """A per-hit 2-D Hough workload, all its events in one call (hits resident): events/s of
+    the whole call and the vote-and-peak kernel's vote rate (hits x columns per second)."""
+    import torch
+    from paper_1305_4855_gb300 import events as ev
+    from paper_1305_4855_gb300.trk import Hough2D
+    cfg = ev.load_workload(workload)
+    batch = ev.make_batch(cfg)
+    h2 = Hough2D(cfg, max_events=batch.n_events, max_hits=batch.n_hits, device=local,
+                 cand_capacity=1 << 22, hit_capacity=1 << 26)
+    hits = torch.from_numpy(batch.packed()).cuda()
+    offs = torch.from_numpy(batch.offsets).cuda()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    tot, vp = [], []
+    for i in range(reps + 2):
+        flush.fill_(i & 0xff)
+        torch.cuda.synchronize()
+        rc = h2.reconstruct_device(hits, offs)
+        assert rc == 0, h2.error()
+        ms = h2.last_ms()
+        if i >= 2:
+            tot.append(ms["total"])
+            vp.append(ms["vote_peak"])
+    n_cand = int(h2.out.n_candidates)
+    h2.close()
+    t, v = float(np.mean(tot)), float(np.mean(vp))
+    votes = batch.n_hits * cfg["hough2d"]["n_cols"]
+    return {"events": batch.n_events, "hits": batch.n_hits, "candidates": n_cand,
+            "call_ms": t, "events_per_s": batch.n_events / (t / 1000.0),
+            "vote_peak_ms": v, "hit_columns_per_s": votes / (v / 1000.0),
+            "l2": "flushed before each call (512 MB write)"}
 
 
 def run_served(args, cfg, batch, capacity, local):

@@ -103,6 +103,8 @@ typedef struct trk_options {
     int32_t use_graph;                      /* capture each call shape in a CUDA graph */
     int32_t vote_level;                     /* vote kernel occupancy: 2, 3 or 4 blocks of 256
                                                threads per SM (0: 3) */
+    int32_t fit_candidates;                 /* 1: fit a helix to every candidate's hits in
+                                               the same call (trk_track, below); 0: skip */
 } trk_options;
 
 /* One candidate (48 bytes). */
@@ -115,6 +117,38 @@ typedef struct trk_candidate {
     float params[5];                        /* bin centre (phi0, q/pT, d0, cot, z0) */
     int32_t reserved;
 } trk_candidate;
+
+/* Fitted helix of one candidate (48 bytes), parallel to the candidates.
+ *
+ * Paper Sec. 8 (with Fig. 6): the candidates found in the parameter space are then fitted
+ * to their hits; the paper times such a fit but does not define it.  The fit here, in
+ * FP64 on the device, one warp per candidate, hits in the candidate's (sorted) order:
+ *   1. algebraic circle fit of all the candidate's hits: (a, b, c) minimising
+ *      sum (u^2 + v^2 + a u + b v + c)^2, (u, v) = (x, y) - centroid, through the 3 x 3
+ *      normal equations; centre = centroid - (a, b)/2, R^2 = a^2/4 + b^2/4 - c;
+ *   2. on each layer only the hit with the smallest | |p - centre| - R | is kept (ties: the
+ *      earlier hit), and the circle is fitted again on the kept hits;
+ *   3. the sense of rotation is the sign of the signed area of the kept hits' polygon in
+ *      layer order (for three hits, D of the triplet); q/pT, phi0, d0 follow as for a
+ *      triplet (perigee about the origin);
+ *   4. signed arc lengths from the perigee as for a triplet, and the least-squares line
+ *      z = z0 + s cot(theta) over the kept hits.
+ * status: TRK_FIT_OK, TRK_FIT_FEW_LAYERS (kept hits on fewer than 3 layers) or
+ * TRK_FIT_DEGENERATE (singular normal equations, centre on the origin, equal arc lengths);
+ * the parameters are zero unless TRK_FIT_OK. */
+#define TRK_FIT_OK 0
+#define TRK_FIT_FEW_LAYERS 1
+#define TRK_FIT_DEGENERATE 2
+
+typedef struct trk_track {
+    float params[5];                        /* phi0, q/pT [1/GeV], d0 [cm], cot(theta), z0 [cm] */
+    float chi2_rphi;                        /* sum over kept hits of (|p - centre| - R)^2 [cm^2] */
+    float chi2_rz;                          /* sum over kept hits of (z - z0 - s cot)^2 [cm^2] */
+    int32_t n_used;                         /* kept hits */
+    int32_t status;                         /* TRK_FIT_* */
+    int32_t event;                          /* event index within the call */
+    uint64_t layers;                        /* bit l set: a hit of layer l was kept */
+} trk_track;
 
 /* Results of one call.  Device arrays and host arrays are owned by the library and
  * stay valid until the next trk_reconstruct* on the same handle or trk_destroy. */
@@ -132,6 +166,11 @@ typedef struct trk_candidates {
     const trk_candidate *h_cand;            /* host copies, filled only by
                                                trk_reconstruct_host (else NULL) */
     const int32_t *h_hit_ids;
+    const trk_track *d_tracks;              /* device [n_candidates] fits when the handle was
+                                               created with fit_candidates, else NULL */
+    const uint8_t *d_hit_used;              /* device [n_hit_ids]: 1 if the fit kept the hit */
+    const trk_track *h_tracks;              /* host copies (trk_reconstruct_host), else NULL */
+    const uint8_t *h_hit_used;
 } trk_candidates;
 
 /* Counters of the last call. */
@@ -218,7 +257,8 @@ int trk_fit_triplets(trk_ctx *h, const trk_hit *hits, int64_t n_hits, const int3
 /* Device time (ms) of the stages of the last call, from CUDA events the library records on
  * the call's stream: ms[0] the vote kernel (triplet fit + vote), ms[1] argument copy,
  * histogram clear, packing and scheduling, ms[2] the peak finder, ms[3] candidate emission,
- * ms[4] hit assignment, compaction and the result copies; ms[5..7] = 0.  Synchronises. */
+ * ms[4] hit assignment and compaction, ms[5] the candidate fit (when enabled) and the
+ * result copies; ms[6..7] = 0.  Synchronises. */
 int trk_profile_stages(trk_ctx *h, float ms[8], void *stream);
 
 /* ---- serving: continuous batching of events that arrive one at a time ------------------
@@ -297,6 +337,124 @@ int trk_server_destroy(trk_server *s);
  * serialized by the caller. */
 int trk_find_peaks_noalloc(const int32_t *hist, int32_t n_events, const trk_binning *binning,
                            uint32_t *cand_bits, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Per-hit 2-D Hough transforms (the paper's own demonstrations)
+ *
+ * TRK2D_STRAIGHT -- Sec. 7 and Fig. 3: each hit of a straight track maps to a sinusoid in
+ *   the (theta, rho) space of lines x cos(theta) + y sin(theta) = rho; peaks are tracks.
+ *   Column c: theta_c = (c + 1/2) pi / n_cols; a hit votes in each column for the row of
+ *   rho = x cos(theta_c) + y sin(theta_c).  Columns wrap with the row mirrored (theta and
+ *   theta + pi are the same line with rho negated), so the rho range must be symmetric.
+ * TRK2D_CURVED_IP -- Sec. 8 and Fig. 5: curved tracks constrained to the interaction point,
+ *   a 2-D space like the straight case.  Column c: phi0_c = -pi + (c + 1/2) 2 pi / n_cols;
+ *   a hit votes for the q/pT of the circle through the origin and the hit that leaves the
+ *   origin in direction phi0_c: q/pT = 2 (x sin(phi0_c) - y cos(phi0_c)) / (K B (x^2 + y^2)),
+ *   K = 0.299792458e-2 GeV/(T cm) (positive charges turn clockwise).  Columns wrap.
+ * Both: row j = floor((v - lo) / ((hi - lo) / n_rows)), a vote iff lo <= v < hi; one
+ * histogram of n_cols x n_rows int32 per event, bin = c * n_rows + j.  A bin is a candidate
+ * iff h >= threshold, h >= each of its 8 neighbours and h > each neighbour with a smaller
+ * bin number (rows outside the range have no neighbour; columns wrap as above).  A
+ * candidate's hits are the hits that voted in its bin.  Hits use only x and y; layer and z
+ * are ignored.  FP32 on the device.
+ *
+ * Vertices (TRK2D_STRAIGHT only, vertex_bins > 0) -- the paper's new trigger capability for
+ * displaced jets: the track peaks of a jet lie on one sinusoid of (theta, rho), the sinusoid
+ * of the jet's vertex, and a second Hough transform over the peaks finds it.  Each candidate
+ * with votes >= vertex_min_votes draws its line x cos(theta) + y sin(theta) = rho (bin
+ * centres, FP64) into a vertex_bins x vertex_bins grid over [-vertex_range, vertex_range)^2
+ * (cell centres g_a = -range + (a + 1/2) w): once per x column in the row of
+ * y = (rho - g_a cos(theta)) / sin(theta) when |sin(theta)| >= |cos(theta)|, else once per y
+ * row in the column of x = (rho - g_b sin(theta)) / cos(theta).  Cell (a, b) has index
+ * a * vertex_bins + b; vertices are the cells passing the 2-D peak rule (8 neighbours, no
+ * wrap) with vertex_threshold; a vertex's tracks are the candidates that voted in its cell.
+ * --------------------------------------------------------------------------------------- */
+#define TRK2D_STRAIGHT 0
+#define TRK2D_CURVED_IP 1
+
+typedef struct trk2d_config {
+    int32_t kind;                           /* TRK2D_* */
+    int32_t n_cols;                         /* theta / phi0 bins, 3 .. 65536 */
+    int32_t n_rows;                         /* rho / q/pT bins, 2 .. 16384 */
+    int32_t threshold;                      /* >= 1 */
+    double lo, hi;                          /* row range (cm, or 1/GeV) */
+    double b_tesla;                         /* field (TRK2D_CURVED_IP) */
+    int32_t max_events;                     /* events per call */
+    int32_t reserved;
+    int64_t max_hits;                       /* hits per call */
+    int64_t cand_capacity;                  /* candidates per call */
+    int64_t hit_capacity;                   /* sum over candidates of their hits per call */
+    int32_t vertex_bins;                    /* 0: no vertex transform; else 3 .. 128 */
+    int32_t vertex_threshold;               /* >= 1 */
+    int32_t vertex_min_votes;               /* candidates below it draw no line */
+    int32_t max_vertices;                   /* per event, <= 1024 */
+    double vertex_range;                    /* cm */
+} trk2d_config;
+
+#define TRK2D_VERTEX_MAX_TRACKS 64          /* tracks listed per vertex */
+
+typedef struct trk2d_vertex {               /* 32 bytes */
+    uint32_t cell;                          /* a * vertex_bins + b */
+    int32_t event;
+    int32_t votes;                          /* candidate lines through the cell */
+    int32_t n_tracks;                       /* listed: min(votes, TRK2D_VERTEX_MAX_TRACKS) */
+    float xy[2];                            /* cell centre (cm) */
+    int64_t track_off;                      /* its tracks: vertex_tracks[track_off ..
+                                               track_off + n_tracks), candidate indices into
+                                               d_cand, ascending */
+} trk2d_vertex;
+
+typedef struct trk2d_candidate {            /* 32 bytes */
+    uint32_t bin;                           /* c * n_rows + j */
+    int32_t event;
+    int32_t votes;                          /* = number of hits */
+    int32_t reserved;
+    int64_t hit_off;                        /* offset of its hits in hit_ids */
+    float params[2];                        /* column centre (theta or phi0), row centre */
+} trk2d_candidate;
+
+typedef struct trk2d_result {
+    int32_t n_events;
+    int64_t n_candidates;
+    int64_t n_hit_ids;
+    const int64_t *cand_off;                /* host [n_events + 1] */
+    const trk2d_candidate *d_cand;          /* device, sorted by (event, bin) */
+    const int32_t *d_hit_ids;               /* device: input hit indices (global), sorted per
+                                               candidate */
+    int64_t n_vertices;                     /* total over the call (0 without vertex_bins) */
+    const int64_t *vertex_off;              /* host [n_events + 1] */
+    const trk2d_vertex *d_vertices;         /* device, sorted by (event, cell) */
+    const int32_t *d_vertex_tracks;         /* device */
+    int32_t vertex_overflow;                /* 1: some event had more than max_vertices (its
+                                               list holds the first max_vertices by cell) */
+} trk2d_result;
+
+typedef struct trk2d_ctx trk2d_ctx;
+
+/* Validates the configuration and allocates every buffer on `device`.  TRK_ERR_INVALID on a
+ * bad configuration (trk_last_error(NULL) says which), TRK_ERR_NOMEM, TRK_ERR_CUDA. */
+int trk2d_create(trk2d_ctx **out, const trk2d_config *config, int32_t device);
+
+/* Histogram, peaks and hit lists for a batch of events: hits and event_offsets are DEVICE
+ * buffers as for trk_reconstruct; outputs are library-owned and valid until the next call
+ * on the handle.  TRK_ERR_INVALID on bad arguments (more events or hits than configured),
+ * TRK_ERR_CAPACITY when the candidates or their hits overflowed (the outputs are then
+ * empty).  Runs on `stream` (NULL: the handle's own), then synchronises it. */
+int trk2d_reconstruct(trk2d_ctx *h, const trk_hit *hits, int64_t n_hits,
+                      const int64_t *event_offsets, int32_t n_events, trk2d_result *out,
+                      void *stream);
+
+/* Copy event e's histogram of the last call (n_cols x n_rows int32, DEVICE dst).
+ * Synchronous. */
+int trk2d_get_histogram(trk2d_ctx *h, int32_t event, int32_t *dst, void *stream);
+
+/* Device time (ms) of the last call's vote-and-peak kernel and of the whole call. */
+int trk2d_last_ms(trk2d_ctx *h, float *vote_peak_ms, float *total_ms);
+
+/* Text of the last error on a 2-D handle (NULL: of the last failed trk2d_create). */
+const char *trk2d_last_error(const trk2d_ctx *h);
+
+int trk2d_destroy(trk2d_ctx *h);
 
 /* Text of the last error on this handle (h NULL: of the last failed trk_create or
  * trk_find_peaks_noalloc). */

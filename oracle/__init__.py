@@ -6,8 +6,10 @@ the CUDA path produced as an input.
 
   enumerate_batch  -- the C definition (trk_oracle.c): every triplet of every listed
                       layer triple, FP64 helix fit, binning, edge-ambiguity flags;
-  reconstruct      -- votes, peak rule and hit assignment (reconstruct.py, numpy).
+  reconstruct      -- votes, peak rule and hit assignment (reconstruct.py, numpy);
+  fit_tracks       -- the candidate fit (trk_oracle.c): algebraic circle fit, one hit per
+                      layer, signed arcs and the least-squares line.
 """
-from .core import OracleSetup, enumerate_batch, fit_list, max_threads  # noqa: F401
+from .core import OracleSetup, enumerate_batch, fit_list, fit_tracks, max_threads  # noqa: F401
 from .reconstruct import (histogram, neighbour_offsets, peaks, assign_hits,  # noqa: F401
                           reconstruct)

@@ -24,6 +24,12 @@ def _load():
         lib.orc_fit_list.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.orc_max_threads.restype = C.c_int32
+        lib.orc_fit_track.restype = C.c_int
+        lib.orc_fit_track.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.orc_fit_tracks.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
+                                       C.c_double, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]
         _lib = lib
     return _lib
 
@@ -161,3 +167,45 @@ def fit_one(p1, p2, p3, b_tesla: float):
     rc = lib.orc_fit(a.ctypes.data, b.ctypes.data, c.ctypes.data, C.c_double(b_tesla),
                      par.ctypes.data)
     return None if rc != 0 else par
+
+
+def fit_tracks(xyz, layer, hit_lists, b_tesla: float, eps_rel: float = 1e-5,
+               n_threads: int = 0) -> dict:
+    """Candidate fits (trk_oracle.c, orc_fit_track) of the given hit lists (each a sequence
+    of global input hit indices, in the order the fit reads them)."""
+    lib = _load()
+    hits = _hits_struct(xyz, layer)
+    off = np.zeros(len(hit_lists) + 1, dtype=np.int64)
+    for t, h in enumerate(hit_lists):
+        off[t + 1] = off[t] + len(h)
+    ids = (np.concatenate([np.asarray(h, dtype=np.int64) for h in hit_lists])
+           if len(hit_lists) and off[-1] else np.zeros(0, dtype=np.int64))
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    n = len(hit_lists)
+    use = np.zeros(max(int(off[-1]), 1), dtype=np.uint8)
+    par = np.zeros((n, 5), dtype=np.float64)
+    chi2 = np.zeros((n, 2), dtype=np.float64)
+    status = np.zeros(n, dtype=np.int32)
+    amb = np.zeros(n, dtype=np.int32)
+    lib.orc_fit_tracks(hits.ctypes.data, ids.ctypes.data, off.ctypes.data, C.c_int64(n),
+                       C.c_double(b_tesla), C.c_double(eps_rel), C.c_int32(n_threads),
+                       use.ctypes.data, par.ctypes.data, chi2.ctypes.data, status.ctypes.data,
+                       amb.ctypes.data)
+    return dict(par=par, chi2=chi2, status=status, amb=amb,
+                use=[use[off[t]:off[t + 1]].astype(bool) for t in range(n)])
+
+
+def fit_track_points(xyz, layer, b_tesla: float, eps_rel: float = 1e-5) -> dict:
+    """The candidate fit of one hit list given as double-precision points (pins)."""
+    lib = _load()
+    pts = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    lay = np.ascontiguousarray(layer, dtype=np.int32)
+    n = len(pts)
+    use = np.zeros(max(n, 1), dtype=np.uint8)
+    par = np.zeros(5, dtype=np.float64)
+    chi2 = np.zeros(2, dtype=np.float64)
+    amb = np.zeros(1, dtype=np.int32)
+    st = lib.orc_fit_track(pts.ctypes.data, lay.ctypes.data, n, C.c_double(b_tesla),
+                           C.c_double(eps_rel), use.ctypes.data, par.ctypes.data,
+                           chi2.ctypes.data, amb.ctypes.data)
+    return dict(status=int(st), par=par, chi2=chi2, amb=int(amb[0]), use=use[:n].astype(bool))

@@ -461,3 +461,242 @@ int32_t orc_max_threads(void)
     return 1;
 #endif
 }
+
+/* ---------------------------------------------------------------------------------------
+ * Candidate fit (Sec. 8: the candidates found in the parameter space are then fitted to
+ * their hits; Fig. 6 times such a fit on CPU cores).  The paper defines no fit; the stated
+ * reading, computed here in double precision from the float32 hits, one candidate at a
+ * time, hits in the order given (the candidate's sorted hit ids):
+ *   1. circle: (a, b, c) minimise sum_k (w_k + a u_k + b v_k + c)^2 over the hits, with
+ *      (u, v) = (x, y) - centroid and w = u^2 + v^2 (the algebraic, Kasa, circle fit; the
+ *      centroid shift changes the minimiser only by the translation), solved through its
+ *      3 x 3 normal equations by Cramer's rule.  Centre = centroid - (a, b)/2,
+ *      R = sqrt(a^2/4 + b^2/4 - c).
+ *   2. hit selection: with the circle of all hits, each layer keeps only its hit with the
+ *      smallest | |p - centre| - R | (ties: the earlier hit); the circle is fitted again
+ *      on the kept hits.
+ *   3. sense: sgn = sign of twice the signed area of the polygon of the kept hits taken in
+ *      layer order, sum_k p_k x p_k+1 closing back to the first (+ when 0); for three hits
+ *      it is D of the triplet.  q/pT = -sgn / (K B R); perigee, phi0 and d0 as for a
+ *      triplet, with |c|^2 - R^2 evaluated directly.
+ *   4. s_k as for a triplet; (cot, z0) = least-squares line z = z0 + s cot over the kept
+ *      hits.
+ *   chi2_rphi = sum (|p - centre| - R)^2 and chi2_rz = sum (z - z0 - s cot)^2 over the kept
+ *   hits.  status: 0 ok, 1 fewer than 3 layers, 2 degenerate (singular normal equations,
+ *   centre on the origin, or all s equal).  amb: bit 0 a layer's two smallest residuals
+ *   lie within eps_rel * R of each other (the selection is ambiguous), bit 2 a hit lies
+ *   within eps_rel * pi of the point opposite the perigee.
+ * --------------------------------------------------------------------------------------- */
+
+static int circle_fit(const double *xyz, const uint8_t *use, int n, double *cx, double *cy,
+                      double *R)
+{
+    double mx = 0.0, my = 0.0;
+    int m = 0;
+    for (int k = 0; k < n; ++k)
+        if (use[k]) {
+            mx += xyz[3 * k];
+            my += xyz[3 * k + 1];
+            ++m;
+        }
+    if (m < 3)
+        return 1;
+    mx /= m;
+    my /= m;
+    double suu = 0, suv = 0, svv = 0, su = 0, sv = 0, sw = 0, suw = 0, svw = 0;
+    for (int k = 0; k < n; ++k) {
+        if (!use[k])
+            continue;
+        const double u = xyz[3 * k] - mx, v = xyz[3 * k + 1] - my, w = u * u + v * v;
+        suu += u * u;
+        suv += u * v;
+        svv += v * v;
+        su += u;
+        sv += v;
+        sw += w;
+        suw += u * w;
+        svw += v * w;
+    }
+    /* normal equations M (a, b, c) = r */
+    const double M[3][3] = {{suu, suv, su}, {suv, svv, sv}, {su, sv, (double)m}};
+    const double r[3] = {-suw, -svw, -sw};
+    const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                       M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                       M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    if (det == 0.0)
+        return 2;
+    double sol[3];
+    for (int col = 0; col < 3; ++col) {
+        double A[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                A[i][j] = (j == col) ? r[i] : M[i][j];
+        sol[col] = (A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                    A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                    A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0])) / det;
+    }
+    const double r2 = sol[0] * sol[0] / 4.0 + sol[1] * sol[1] / 4.0 - sol[2];
+    if (!(r2 > 0.0))
+        return 2;
+    *cx = mx - sol[0] / 2.0;
+    *cy = my - sol[1] / 2.0;
+    *R = sqrt(r2);
+    return 0;
+}
+
+int orc_fit_track(const double *xyz, const int32_t *layer, int n, double b_tesla,
+                  double eps_rel, uint8_t *use, double *par, double *chi2, int32_t *amb)
+{
+    *amb = 0;
+    for (int k = 0; k < n; ++k)
+        use[k] = 1;
+    double cx, cy, R;
+    int st = circle_fit(xyz, use, n, &cx, &cy, &R);
+    if (st) {
+        for (int k = 0; k < n; ++k)
+            use[k] = 0;      /* no circle: nothing is kept */
+        return st;
+    }
+    /* per layer, keep the hit closest to the circle */
+    for (int k = 0; k < n; ++k)
+        use[k] = 0;
+    int n_layers_used = 0;
+    for (int k = 0; k < n; ++k) {
+        int seen = 0;
+        for (int j = 0; j < k; ++j)
+            if (layer[j] == layer[k])
+                seen = 1;
+        if (seen)
+            continue;
+        int best = -1;
+        double rb = 0.0, second = INFINITY;
+        for (int j = k; j < n; ++j) {
+            if (layer[j] != layer[k])
+                continue;
+            const double dx = xyz[3 * j] - cx, dy = xyz[3 * j + 1] - cy;
+            const double res = fabs(sqrt(dx * dx + dy * dy) - R);
+            if (best < 0 || res < rb) {
+                if (best >= 0)
+                    second = rb;
+                best = j;
+                rb = res;
+            } else if (res < second) {
+                second = res;
+            }
+        }
+        if (second - rb <= eps_rel * R)
+            *amb |= 1;
+        use[best] = 1;
+        ++n_layers_used;
+    }
+    if (n_layers_used < 3)
+        return 1;
+    st = circle_fit(xyz, use, n, &cx, &cy, &R);
+    if (st)
+        return st;
+    /* sense of rotation: twice the signed area of the polygon of the kept hits taken in
+     * layer order (for three hits this is D of the triplet) */
+    double area2 = 0.0;
+    int first = -1, prev = -1;
+    for (int L = 0; L < 64; ++L)
+        for (int k = 0; k < n; ++k) {
+            if (!use[k] || layer[k] != L)
+                continue;
+            if (first < 0)
+                first = k;
+            else
+                area2 += xyz[3 * prev] * xyz[3 * k + 1] - xyz[3 * prev + 1] * xyz[3 * k];
+            prev = k;
+        }
+    area2 += xyz[3 * prev] * xyz[3 * first + 1] - xyz[3 * prev + 1] * xyz[3 * first];
+    const double sgn = area2 >= 0.0 ? 1.0 : -1.0;
+    const double cn = sqrt(cx * cx + cy * cy);
+    if (cn == 0.0)
+        return 2;
+    const double power = cx * cx + cy * cy - R * R;
+    const double cn_minus_r = power / (cn + R);
+    const double px = cx * (cn_minus_r / cn), py = cy * (cn_minus_r / cn);
+    const double phi0 = atan2(-sgn * cx, sgn * cy);
+    const double d0 = -px * sin(phi0) + py * cos(phi0);
+    const double qopt = -sgn / (ORC_K * b_tesla * R);
+    /* signed arcs from the perigee and the least-squares line */
+    const double tx = cos(phi0), ty = sin(phi0);
+    double sbar = 0.0, zbar = 0.0;
+    int m = 0;
+    double *s = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int k = 0; k < n; ++k) {
+        if (!use[k])
+            continue;
+        const double dx = xyz[3 * k] - px, dy = xyz[3 * k + 1] - py;
+        double a = sqrt(dx * dx + dy * dy) / (2.0 * R);
+        if (a > 1.0)
+            a = 1.0;
+        const double half = asin(a);
+        if (2.0 * half >= ORC_PI * (1.0 - eps_rel))
+            *amb |= 4;
+        s[k] = ((dx * tx + dy * ty) >= 0.0 ? 1.0 : -1.0) * 2.0 * R * half;
+        sbar += s[k];
+        zbar += xyz[3 * k + 2];
+        ++m;
+    }
+    sbar /= m;
+    zbar /= m;
+    double sss = 0.0, ssz = 0.0;
+    for (int k = 0; k < n; ++k)
+        if (use[k]) {
+            sss += (s[k] - sbar) * (s[k] - sbar);
+            ssz += (s[k] - sbar) * (xyz[3 * k + 2] - zbar);
+        }
+    if (sss == 0.0) {
+        free(s);
+        return 2;
+    }
+    const double cot = ssz / sss, z0 = zbar - cot * sbar;
+    double c2r = 0.0, c2z = 0.0;
+    for (int k = 0; k < n; ++k)
+        if (use[k]) {
+            const double dx = xyz[3 * k] - cx, dy = xyz[3 * k + 1] - cy;
+            const double rr = sqrt(dx * dx + dy * dy) - R;
+            const double rz = xyz[3 * k + 2] - z0 - cot * s[k];
+            c2r += rr * rr;
+            c2z += rz * rz;
+        }
+    free(s);
+    par[0] = phi0;
+    par[1] = qopt;
+    par[2] = d0;
+    par[3] = cot;
+    par[4] = z0;
+    chi2[0] = c2r;
+    chi2[1] = c2z;
+    return 0;
+}
+
+/* Fit many candidates: hit lists concatenated in ids (indices into hits), candidate t
+ * owns ids[off[t] .. off[t+1]).  use is parallel to ids. */
+void orc_fit_tracks(const orc_hit *hits, const int64_t *ids, const int64_t *off, int64_t n_cand,
+                    double b_tesla, double eps_rel, int32_t n_threads, uint8_t *use,
+                    double *par, double *chi2, int32_t *status, int32_t *amb)
+{
+#ifdef _OPENMP
+    if (n_threads > 0)
+        omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (int64_t t = 0; t < n_cand; ++t) {
+        const int n = (int)(off[t + 1] - off[t]);
+        double *xyz = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+        int32_t *lay = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        for (int k = 0; k < n; ++k) {
+            const orc_hit *h = hits + ids[off[t] + k];
+            xyz[3 * k] = h->x;
+            xyz[3 * k + 1] = h->y;
+            xyz[3 * k + 2] = h->z;
+            lay[k] = h->layer;
+        }
+        status[t] = orc_fit_track(xyz, lay, n, b_tesla, eps_rel, use + off[t], par + 5 * t,
+                                  chi2 + 2 * t, amb + t);
+        free(xyz);
+        free(lay);
+    }
+}

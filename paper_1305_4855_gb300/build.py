@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtrk.so")
 SOURCES = ["trk_vote.cu", "trk_vote_l2.cu", "trk_vote_l3.cu", "trk_vote_l4.cu", "trk_pipeline.cu",
-           "trk_api.cu", "trk_noalloc.cu", "trk_serve.cu"]
+           "trk_api.cu", "trk_noalloc.cu", "trk_serve.cu", "trk_fit.cu",
+           "trk_hough2d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -44,6 +44,11 @@ cudaError_t launch_vote_offsets(const trk_candidate *cand, const unsigned long l
                                 int64_t cand_cap, int64_t *vote_off, int64_t *bsum,
                                 unsigned long long *total, cudaStream_t s);
 cudaError_t launch_assign(const AssignArgs &A, int n_sm, cudaStream_t s);
+cudaError_t launch_cand_fit(const trk_candidate *cand, const unsigned long long *n_cand,
+                            int64_t cand_cap, const int32_t *hit_ids, int64_t hit_cap,
+                            const CallArgs *args, double kB, int n_layers, trk_track *out,
+                            uint8_t *hit_used, int n_sm, cudaStream_t s);
+cudaError_t prepare_fit_kernel();
 cudaError_t launch_cand_hits(const trk_candidate *cand, const unsigned long long *n_cand,
                              int64_t cand_cap, const int64_t *vote_off, int32_t *assign,
                              int64_t assign_cap, const CallArgs *args, int32_t *nhits,
@@ -113,6 +118,8 @@ struct trk_ctx {
     int32_t *d_nhits = nullptr;
     int64_t *d_hit_off = nullptr;
     int32_t *d_hit_ids = nullptr;
+    trk_track *d_tracks = nullptr;       // candidate fits (fit_candidates)
+    uint8_t *d_hit_used = nullptr;       // per hit id: kept by the fit
     int64_t *d_cand_off = nullptr;
     trk_hit *d_in_hits = nullptr;
     int64_t *d_in_offsets = nullptr;
@@ -124,10 +131,12 @@ struct trk_ctx {
     int32_t *h_status = nullptr;
     trk_candidate *h_cand = nullptr;
     int32_t *h_hit_ids = nullptr;
+    trk_track *h_tracks = nullptr;
+    uint8_t *h_hit_used = nullptr;
 
     std::map<int, cudaGraphExec_t> graphs;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    cudaEvent_t ev_st[4] = {nullptr, nullptr, nullptr, nullptr};  // stage boundaries
+    cudaEvent_t ev_st[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stage boundaries
     cudaStream_t own_stream = nullptr;   // used when the caller passes the legacy stream
     trk_stats stats;
     int last_n_events = 0;
@@ -286,11 +295,13 @@ static void free_all(trk_ctx *h)
                    h->d_cbits,     h->d_filter,     h->d_wprefix,
                    h->d_bsum,      h->d_cand,       h->d_fill,        h->d_vote_off, h->d_assign,
                    h->d_nhits,     h->d_hit_off,    h->d_hit_ids,     h->d_cand_off, h->d_in_hits,
+                   h->d_tracks,    h->d_hit_used,
                    h->d_in_offsets, h->d_chunk_pos};
     for (void *p : dev)
         if (p)
             cudaFree(p);
-    void *host[] = {h->h_args, h->h_ctr, h->h_cand_off, h->h_status, h->h_cand, h->h_hit_ids};
+    void *host[] = {h->h_args,  h->h_ctr,     h->h_cand_off, h->h_status,
+                    h->h_cand,  h->h_hit_ids, h->h_tracks,   h->h_hit_used};
     for (void *p : host)
         if (p)
             cudaFreeHost(p);
@@ -449,6 +460,10 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
     ALLOC(d_nhits, o.cand_capacity);
     ALLOC(d_hit_off, o.cand_capacity);
     ALLOC(d_hit_ids, o.assign_capacity);
+    if (o.fit_candidates) {
+        ALLOC(d_tracks, o.cand_capacity);
+        ALLOC(d_hit_used, o.assign_capacity);
+    }
     ALLOC(d_cand_off, E + 1);
 #undef ALLOC
     if (cudaMallocHost((void **)&h->h_args, sizeof(CallArgs)) != cudaSuccess ||
@@ -465,7 +480,8 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
         cudaStreamCreate(&h->own_stream) != cudaSuccess ||
         cudaEventCreate(&h->ev_st[0]) != cudaSuccess || cudaEventCreate(&h->ev_st[1]) != cudaSuccess ||
         cudaEventCreate(&h->ev_st[2]) != cudaSuccess || cudaEventCreate(&h->ev_st[3]) != cudaSuccess ||
-        prepare_pipeline_kernels() != cudaSuccess ||
+        cudaEventCreate(&h->ev_st[4]) != cudaSuccess ||
+        prepare_pipeline_kernels() != cudaSuccess || prepare_fit_kernel() != cudaSuccess ||
         cudaMemset(h->d_hist, 0, sizeof(int32_t) * (size_t)(E * h->nbins)) != cudaSuccess ||
         cudaMemset(h->d_chunk_item, 0xff, sizeof(int32_t) * (size_t)h->chunk_cap) != cudaSuccess ||
         cudaMemset(h->d_chunk_count, 0, sizeof(int32_t) * (size_t)h->chunk_cap) != cudaSuccess ||
@@ -576,6 +592,11 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     TRK_CUDA(h, launch_compact(h->d_cand, &ctr->n_cand, o.cand_capacity, h->d_vote_off,
                                h->d_assign, h->d_nhits, h->d_hit_off, h->d_ev_begin,
                                h->d_hit_ids, h->n_sm, s));
+    TRK_CUDA(h, mark(h->ev_st[4]));
+    if (o.fit_candidates)
+        TRK_CUDA(h, launch_cand_fit(h->d_cand, &ctr->n_cand, o.cand_capacity, h->d_hit_ids,
+                                    o.assign_capacity, h->d_args, h->C.kB_d, h->geo.n_layers,
+                                    h->d_tracks, h->d_hit_used, h->n_sm, s));
     TRK_CUDA(h, launch_finalize(h->d_wprefix, h->W, h->d_args, ctr, o.cand_capacity,
                                 h->d_cand_off, h->d_status, s));
     TRK_CUDA(h, cudaMemcpyAsync(h->h_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
@@ -646,6 +667,10 @@ static int finish_call(trk_ctx *h, int n_events, trk_candidates *out, cudaStream
         out->d_hit_ids = h->d_hit_ids;
         out->h_cand = nullptr;
         out->h_hit_ids = nullptr;
+        out->d_tracks = h->d_tracks;
+        out->d_hit_used = h->d_hit_used;
+        out->h_tracks = nullptr;
+        out->h_hit_used = nullptr;
     }
     if (over)
         return fail(h, TRK_ERR_CAPACITY, "candidate or assignment capacity exceeded");
@@ -708,6 +733,11 @@ extern "C" int trk_reconstruct_host(trk_ctx *h, const trk_hit *hits, int64_t n_h
             cudaMallocHost((void **)&h->h_hit_ids, sizeof(int32_t) * h->opt.assign_capacity) !=
                 cudaSuccess)
             return fail(h, TRK_ERR_NOMEM, "pinned result allocation failed");
+        if (h->opt.fit_candidates &&
+            (cudaMallocHost((void **)&h->h_tracks, sizeof(trk_track) * h->opt.cand_capacity) !=
+                 cudaSuccess ||
+             cudaMallocHost((void **)&h->h_hit_used, (size_t)h->opt.assign_capacity) != cudaSuccess))
+            return fail(h, TRK_ERR_NOMEM, "pinned result allocation failed");
     }
     TRK_CUDA(h, cudaEventRecord(h->ev0, s));
     if (n_hits > 0)
@@ -733,11 +763,19 @@ extern "C" int trk_reconstruct_host(trk_ctx *h, const trk_hit *hits, int64_t n_h
         if (c.n_hit_ids > 0)
             TRK_CUDA(h, cudaMemcpyAsync(h->h_hit_ids, h->d_hit_ids, sizeof(int32_t) * c.n_hit_ids,
                                         cudaMemcpyDeviceToHost, s));
+        if (h->opt.fit_candidates && c.n_cand > 0)
+            TRK_CUDA(h, cudaMemcpyAsync(h->h_tracks, h->d_tracks, sizeof(trk_track) * c.n_cand,
+                                        cudaMemcpyDeviceToHost, s));
+        if (h->opt.fit_candidates && c.n_hit_ids > 0)
+            TRK_CUDA(h, cudaMemcpyAsync(h->h_hit_used, h->d_hit_used, (size_t)c.n_hit_ids,
+                                        cudaMemcpyDeviceToHost, s));
     }
     rc = finish_call(h, n_events, out, s);
     if (out) {
         out->h_cand = h->h_cand;
         out->h_hit_ids = h->h_hit_ids;
+        out->h_tracks = h->h_tracks;
+        out->h_hit_used = h->h_hit_used;
     }
     return rc;
 }
@@ -829,7 +867,8 @@ extern "C" int trk_profile_stages(trk_ctx *h, float ms[8], void *stream)
     TRK_CUDA(h, cudaEventElapsedTime(&ms[1], h->ev0, h->ev_st[0]));
     TRK_CUDA(h, cudaEventElapsedTime(&ms[2], h->ev_st[1], h->ev_st[2]));
     TRK_CUDA(h, cudaEventElapsedTime(&ms[3], h->ev_st[2], h->ev_st[3]));
-    TRK_CUDA(h, cudaEventElapsedTime(&ms[4], h->ev_st[3], h->ev1));
+    TRK_CUDA(h, cudaEventElapsedTime(&ms[4], h->ev_st[3], h->ev_st[4]));
+    TRK_CUDA(h, cudaEventElapsedTime(&ms[5], h->ev_st[4], h->ev1));
     return TRK_OK;
 }
 

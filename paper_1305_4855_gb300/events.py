@@ -83,10 +83,17 @@ def concat(batches: list[Batch]) -> Batch:
     xyz = np.concatenate([b.xyz for b in batches]) if batches else np.zeros((0, 3), np.float32)
     layer = np.concatenate([b.layer for b in batches]) if batches else np.zeros(0, np.int32)
     offs = [0]
-    tracks, truths = [], []
+    tracks, truths, verts = [], [], []
     ntr = 0
     ev = 0
     for b in batches:
+        if "vertices" in b.extra:
+            v = np.asarray(b.extra["vertices"], dtype=np.float64).reshape(-1, b.extra["vertices"].shape[-1])
+            if v.shape[1] == 3:               # (x, y, n_tracks) of a single event
+                v = np.concatenate([v, np.zeros((len(v), 1))], axis=1)
+            v = v.copy()
+            v[:, 3] += ev
+            verts.append(v)
         for e in range(b.n_events):
             offs.append(offs[-1] + int(b.offsets[e + 1] - b.offsets[e]))
         t = b.track.copy()
@@ -97,18 +104,32 @@ def concat(batches: list[Batch]) -> Batch:
         truths.append(tr)
         ntr += len(b.truth)
         ev += b.n_events
+    extra = {"vertices": np.concatenate(verts)} if verts else {}
     return Batch(xyz, layer, np.array(offs, dtype=np.int64),
                  np.concatenate(tracks) if tracks else np.zeros(0, np.int32),
-                 np.concatenate(truths) if truths else np.zeros((0, 6)))
+                 np.concatenate(truths) if truths else np.zeros((0, 6)), extra)
 
 
 # ---------------------------------------------------------------------------------------
 # helix propagation (forward model)
 # ---------------------------------------------------------------------------------------
 
+def _line_crossing(sx, sy, psi, r):
+    """Path length t > 0 at which the straight line leaving (sx, sy) in direction psi first
+    reaches radius r (B = 0); inf where it never does."""
+    ux, uy = np.cos(psi), np.sin(psi)
+    su = sx * ux + sy * uy
+    disc = su * su - (sx * sx + sy * sy) + r * r
+    t = -su + np.sqrt(np.maximum(disc, 0.0))
+    return np.where((disc >= 0.0) & (t > 1e-9), t, np.inf)
+
+
 def _first_crossing(sx, sy, psi, kappa, r):
     """Arc length t > 0 at which a circle track leaving (sx, sy) with direction psi and
-    signed curvature kappa first reaches radius r; inf where it never does."""
+    signed curvature kappa first reaches radius r; inf where it never does.  kappa = 0 is a
+    straight line."""
+    if np.all(np.asarray(kappa) == 0.0):
+        return _line_crossing(sx, sy, psi, r)
     cx = sx - np.sin(psi) / kappa
     cy = sy + np.cos(psi) / kappa
     rho = 1.0 / np.abs(kappa)
@@ -134,13 +155,20 @@ def _first_crossing(sx, sy, psi, kappa, r):
 
 
 def _position(sx, sy, psi, kappa, t):
+    if np.all(np.asarray(kappa) == 0.0):
+        return sx + t * np.cos(psi), sy + t * np.sin(psi)
     x = sx + (np.sin(psi + kappa * t) - np.sin(psi)) / kappa
     y = sy - (np.cos(psi + kappa * t) - np.cos(psi)) / kappa
     return x, y
 
 
 def _perigee_from_state(sx, sy, psi, kappa, sz, cot):
-    """Truth perigee parameters of the circle track through (sx, sy) with direction psi."""
+    """Truth perigee parameters of the circle track through (sx, sy) with direction psi
+    (kappa = 0: the straight line)."""
+    if np.all(np.asarray(kappa) == 0.0):
+        d0 = -sx * np.sin(psi) + sy * np.cos(psi)
+        t_ps = sx * np.cos(psi) + sy * np.sin(psi)      # path length from P to the start
+        return np.asarray(psi, dtype=np.float64) + 0.0, d0, sz - cot * t_ps
     cx = sx - np.sin(psi) / kappa
     cy = sy + np.cos(psi) / kappa
     rho = 1.0 / np.abs(kappa)
@@ -161,9 +189,41 @@ def _perigee_from_state(sx, sy, psi, kappa, sz, cot):
     return phi0, d0, z0
 
 
+def _jet_tracks(cfg: dict, rng: np.random.Generator, n_prompt: int):
+    """Prompt tracks plus displaced jets: each jet's tracks leave one vertex (radius in
+    rprod_range, uniform azimuth) within +-cone of the radial direction."""
+    ev = cfg["events"]
+    d = ev["displaced"]
+    n_jets = int(rng.integers(d["n_jets"][0], d["n_jets"][1] + 1))
+    per = [int(rng.integers(d["tracks_per_jet"][0], d["tracks_per_jet"][1] + 1))
+           for _ in range(n_jets)]
+    rp = rng.uniform(d["rprod_range"][0], d["rprod_range"][1], n_jets)
+    phv = rng.uniform(-np.pi, np.pi, n_jets)
+    n = n_prompt + sum(per)
+    sub = dict(cfg, events=dict(ev, displaced={"kind": "none", "fraction": 0.0}))
+    tr = _tracks(sub, rng, n)
+    k = n_prompt
+    vertices = []
+    for j in range(n_jets):
+        sl = slice(k, k + per[j])
+        vx, vy = rp[j] * np.cos(phv[j]), rp[j] * np.sin(phv[j])
+        tr["sx"][sl], tr["sy"][sl] = vx, vy
+        tr["psi"][sl] = phv[j] + rng.uniform(-d["cone"], d["cone"], per[j])
+        tr["r_start"][sl] = rp[j]
+        vertices.append((vx, vy, per[j]))
+        k += per[j]
+    phi0, d0, z0 = _perigee_from_state(tr["sx"], tr["sy"], tr["psi"], tr["kappa"], tr["sz"],
+                                       tr["cot"])
+    tr["truth"] = np.stack([phi0, tr["truth"][:, 1], d0, tr["cot"], z0], axis=1)
+    tr["vertices"] = np.array(vertices, dtype=np.float64).reshape(-1, 3)
+    return tr
+
+
 def _tracks(cfg: dict, rng: np.random.Generator, n_tracks: int):
     ev = cfg["events"]
     B = cfg["geometry"]["b_tesla"]
+    if ev.get("displaced", {}).get("kind") == "jets":
+        return _jet_tracks(cfg, rng, n_tracks)
     lo_pt, hi_pt = ev["pt_range"]
     pt = np.exp(rng.uniform(math.log(lo_pt), math.log(hi_pt), n_tracks))
     q = rng.choice(np.array([-1.0, 1.0]), n_tracks)
@@ -211,6 +271,7 @@ def make_event(cfg: dict, rng: np.random.Generator, n_tracks: int,
     radius = np.asarray(geo["radius"], dtype=np.float64)
     zhalf = np.asarray(geo["z_half"], dtype=np.float64)
     tr = _tracks(cfg, rng, n_tracks)
+    n_tracks = len(tr["truth"])
     xs, ys, zs, ls, ts = [], [], [], [], []
     alive = np.ones(n_tracks, dtype=bool)
     for L, (r, zh) in enumerate(zip(radius, zhalf)):
@@ -248,8 +309,9 @@ def make_event(cfg: dict, rng: np.random.Generator, n_tracks: int,
         x, y, z, lay, trk = x[perm], y[perm], z[perm], lay[perm], trk[perm]
     xyz = np.stack([x, y, z], axis=1).astype(np.float32)
     truth = np.concatenate([tr["truth"], np.zeros((n_tracks, 1))], axis=1)
+    extra = {"vertices": tr["vertices"]} if "vertices" in tr else {}
     return Batch(xyz, lay.astype(np.int32), np.array([0, len(x)], dtype=np.int64),
-                 trk.astype(np.int32), truth)
+                 trk.astype(np.int32), truth, extra)
 
 
 def track_counts(cfg: dict, rng: np.random.Generator, n_events: int) -> np.ndarray:

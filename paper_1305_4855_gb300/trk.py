@@ -28,7 +28,10 @@ EXPORTED = ["trk_options_default", "trk_create", "trk_reconstruct", "trk_reconst
             "trk_get_votes", "trk_fit_triplets", "trk_profile_stages", "trk_last_error", "trk_version",
             "trk_autotune",
             "trk_find_peaks_noalloc", "trk_server_create", "trk_server_submit", "trk_server_wait",
-            "trk_server_take", "trk_server_counts", "trk_server_destroy"]
+            "trk_server_take", "trk_server_counts", "trk_server_destroy",
+            "trk2d_create", "trk2d_reconstruct", "trk2d_get_histogram", "trk2d_last_ms",
+            "trk2d_last_error", "trk2d_destroy"]
+TRK2D_STRAIGHT, TRK2D_CURVED_IP = 0, 1
 
 
 class trk_geometry(C.Structure):
@@ -48,7 +51,7 @@ class trk_options(C.Structure):
                 ("cand_capacity", C.c_int64), ("assign_capacity", C.c_int64),
                 ("peak_scratch_bytes", C.c_int64), ("tile_i", C.c_int32), ("tile_j", C.c_int32),
                 ("k_chunk", C.c_int32), ("blocks_per_sm", C.c_int32), ("use_graph", C.c_int32),
-                ("vote_level", C.c_int32)]
+                ("vote_level", C.c_int32), ("fit_candidates", C.c_int32)]
 
 
 class trk_candidate(C.Structure):
@@ -61,7 +64,49 @@ class trk_candidates(C.Structure):
     _fields_ = [("n_events", C.c_int32), ("n_candidates", C.c_int64), ("n_hit_ids", C.c_int64),
                 ("cand_off", C.POINTER(C.c_int64)), ("status", C.POINTER(C.c_int32)),
                 ("d_cand", C.c_void_p), ("d_hit_ids", C.c_void_p), ("h_cand", C.c_void_p),
-                ("h_hit_ids", C.c_void_p)]
+                ("h_hit_ids", C.c_void_p), ("d_tracks", C.c_void_p), ("d_hit_used", C.c_void_p),
+                ("h_tracks", C.c_void_p), ("h_hit_used", C.c_void_p)]
+
+
+class trk_track(C.Structure):
+    _fields_ = [("params", C.c_float * 5), ("chi2_rphi", C.c_float), ("chi2_rz", C.c_float),
+                ("n_used", C.c_int32), ("status", C.c_int32), ("event", C.c_int32),
+                ("layers", C.c_uint64)]
+
+
+class trk2d_config(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_cols", C.c_int32), ("n_rows", C.c_int32),
+                ("threshold", C.c_int32), ("lo", C.c_double), ("hi", C.c_double),
+                ("b_tesla", C.c_double), ("max_events", C.c_int32), ("reserved", C.c_int32),
+                ("max_hits", C.c_int64), ("cand_capacity", C.c_int64), ("hit_capacity", C.c_int64),
+                ("vertex_bins", C.c_int32), ("vertex_threshold", C.c_int32),
+                ("vertex_min_votes", C.c_int32), ("max_vertices", C.c_int32),
+                ("vertex_range", C.c_double)]
+
+
+class trk2d_candidate(C.Structure):
+    _fields_ = [("bin", C.c_uint32), ("event", C.c_int32), ("votes", C.c_int32),
+                ("reserved", C.c_int32), ("hit_off", C.c_int64), ("params", C.c_float * 2)]
+
+
+class trk2d_result(C.Structure):
+    _fields_ = [("n_events", C.c_int32), ("n_candidates", C.c_int64), ("n_hit_ids", C.c_int64),
+                ("cand_off", C.POINTER(C.c_int64)), ("d_cand", C.c_void_p),
+                ("d_hit_ids", C.c_void_p), ("n_vertices", C.c_int64),
+                ("vertex_off", C.POINTER(C.c_int64)), ("d_vertices", C.c_void_p),
+                ("d_vertex_tracks", C.c_void_p), ("vertex_overflow", C.c_int32)]
+
+
+class trk2d_vertex(C.Structure):
+    _fields_ = [("cell", C.c_uint32), ("event", C.c_int32), ("votes", C.c_int32),
+                ("n_tracks", C.c_int32), ("xy", C.c_float * 2), ("track_off", C.c_int64)]
+
+
+CAND2D_DTYPE = np.dtype([("bin", "<u4"), ("event", "<i4"), ("votes", "<i4"), ("reserved", "<i4"),
+                         ("hit_off", "<i8"), ("params", "<f4", (2,))])
+VERTEX_DTYPE = np.dtype([("cell", "<u4"), ("event", "<i4"), ("votes", "<i4"), ("n_tracks", "<i4"),
+                         ("xy", "<f4", (2,)), ("track_off", "<i8")])
+TRK2D_VERTEX_MAX_TRACKS = 64
 
 
 class trk_tuning(C.Structure):
@@ -85,6 +130,12 @@ class trk_stats(C.Structure):
 CAND_DTYPE = np.dtype([("bin", "<u4"), ("event", "<i4"), ("votes", "<i4"), ("n_hits", "<i4"),
                        ("hit_off", "<i8"), ("params", "<f4", (5,)), ("reserved", "<i4")])
 assert CAND_DTYPE.itemsize == C.sizeof(trk_candidate) == 48
+# numpy view of trk_track (48 bytes)
+TRACK_DTYPE = np.dtype({"names": ["params", "chi2_rphi", "chi2_rz", "n_used", "status", "event",
+                                  "layers"],
+                        "formats": [("<f4", (5,)), "<f4", "<f4", "<i4", "<i4", "<i4", "<u8"],
+                        "offsets": [0, 20, 24, 28, 32, 36, 40], "itemsize": 48})
+TRK_FIT_OK, TRK_FIT_FEW_LAYERS, TRK_FIT_DEGENERATE = 0, 1, 2
 
 _lib = None
 
@@ -142,6 +193,18 @@ def load_library(path: str = LIB_PATH):
     lib.trk_server_destroy.restype = C.c_int
     lib.trk_version.argtypes = []
     lib.trk_version.restype = C.c_char_p
+    lib.trk2d_create.argtypes = [C.POINTER(vp), vp, i32]
+    lib.trk2d_create.restype = C.c_int
+    lib.trk2d_reconstruct.argtypes = [vp, vp, i64, vp, i32, vp, vp]
+    lib.trk2d_reconstruct.restype = C.c_int
+    lib.trk2d_get_histogram.argtypes = [vp, i32, vp, vp]
+    lib.trk2d_get_histogram.restype = C.c_int
+    lib.trk2d_last_ms.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+    lib.trk2d_last_ms.restype = C.c_int
+    lib.trk2d_last_error.argtypes = [vp]
+    lib.trk2d_last_error.restype = C.c_char_p
+    lib.trk2d_destroy.argtypes = [vp]
+    lib.trk2d_destroy.restype = C.c_int
     _lib = lib
     return lib
 
@@ -217,12 +280,21 @@ class Result:
     cand_off: np.ndarray      # int64 [n_events + 1]
     status: np.ndarray        # int32 [n_events]
     rc: int
+    tracks: np.ndarray = None     # structured TRACK_DTYPE, parallel to cand (fit_candidates)
+    hit_used: np.ndarray = None   # bool, parallel to hit_ids (fit_candidates)
 
     def event(self, e: int):
         a, b = int(self.cand_off[e]), int(self.cand_off[e + 1])
         c = self.cand[a:b]
         hits = [self.hit_ids[int(r["hit_off"]):int(r["hit_off"]) + int(r["n_hits"])] for r in c]
         return c, hits
+
+    def event_fits(self, e: int):
+        """(tracks of event e's candidates, per candidate the bool mask of kept hits)."""
+        a, b = int(self.cand_off[e]), int(self.cand_off[e + 1])
+        c = self.cand[a:b]
+        used = [self.hit_used[int(r["hit_off"]):int(r["hit_off"]) + int(r["n_hits"])] for r in c]
+        return self.tracks[a:b], used
 
 
 class Reconstructor:
@@ -296,17 +368,41 @@ class Reconstructor:
         n_ev = o.n_events
         cand_off = np.ctypeslib.as_array(o.cand_off, shape=(n_ev + 1,)).copy()
         status = np.ctypeslib.as_array(o.status, shape=(n_ev,)).copy()
+        tracks = hit_used = None
         if from_host:
             nb = o.n_candidates * 48
             cand = np.frombuffer((C.c_char * nb).from_address(o.h_cand), dtype=CAND_DTYPE).copy() \
                 if nb else np.zeros(0, CAND_DTYPE)
             hit_ids = np.frombuffer((C.c_char * (4 * o.n_hit_ids)).from_address(o.h_hit_ids),
                                     dtype=np.int32).copy() if o.n_hit_ids else np.zeros(0, np.int32)
+            if o.h_tracks:
+                tracks = np.frombuffer((C.c_char * nb).from_address(o.h_tracks),
+                                       dtype=TRACK_DTYPE).copy() if nb else np.zeros(0, TRACK_DTYPE)
+                hit_used = np.frombuffer((C.c_char * o.n_hit_ids).from_address(o.h_hit_used),
+                                         dtype=np.uint8).astype(bool) if o.n_hit_ids \
+                    else np.zeros(0, bool)
         else:
             cd, hd = self.device_outputs()
             cand = cd.cpu().numpy().view(CAND_DTYPE)
             hit_ids = hd.cpu().numpy()
-        return Result(cand, hit_ids, cand_off, status, rc)
+            if o.d_tracks:
+                tracks, used = self.device_fits()
+                tracks = tracks.cpu().numpy().view(TRACK_DTYPE).reshape(-1)
+                hit_used = used.cpu().numpy().astype(bool)
+        return Result(cand, hit_ids, cand_off, status, rc, tracks, hit_used)
+
+    def device_fits(self):
+        """(tracks uint8 (n, 48), hit_used uint8 (n_hit_ids,)) as torch tensors on the device,
+        cloned out of the library's buffers (needs fit_candidates)."""
+        import torch
+        o = self.out
+        if not o.d_tracks:
+            raise TrkError(TRK_ERR_INVALID, "handle created without fit_candidates")
+        tr = torch.as_tensor(_DevArray(o.d_tracks, (o.n_candidates, 48), "|u1"), device="cuda").clone() \
+            if o.n_candidates else torch.zeros((0, 48), dtype=torch.uint8, device="cuda")
+        used = torch.as_tensor(_DevArray(o.d_hit_used, (o.n_hit_ids,), "|u1"), device="cuda").clone() \
+            if o.n_hit_ids else torch.zeros(0, dtype=torch.uint8, device="cuda")
+        return tr, used
 
     def stats(self) -> dict:
         s = trk_stats()
@@ -329,7 +425,8 @@ class Reconstructor:
         rc = self.lib.trk_profile_stages(self.h, ms, C.c_void_p(_stream_handle(stream)))
         if rc != TRK_OK:
             raise TrkError(rc, self.error())
-        return dict(vote=ms[0], setup=ms[1], peaks=ms[2], candidates=ms[3], assign=ms[4])
+        return dict(vote=ms[0], setup=ms[1], peaks=ms[2], candidates=ms[3], assign=ms[4],
+                    fit=ms[5])
 
     def histogram(self, event: int = 0):
         import torch
@@ -428,6 +525,106 @@ class Server:
         if getattr(self, "s", None):
             self.lib.trk_server_destroy(self.s)
             self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hough2d_config(cfg: dict, max_events: int, max_hits: int, **over) -> trk2d_config:
+    """trk2d_config from a workload's "hough2d" block."""
+    h = cfg["hough2d"]
+    c = trk2d_config()
+    c.kind = TRK2D_STRAIGHT if h["kind"] == "straight" else TRK2D_CURVED_IP
+    c.n_cols, c.n_rows, c.threshold = int(h["n_cols"]), int(h["n_rows"]), int(h["threshold"])
+    c.lo, c.hi = float(h["lo"]), float(h["hi"])
+    c.b_tesla = float(cfg["geometry"].get("b_tesla", 0.0))
+    c.max_events, c.max_hits = int(max_events), int(max_hits)
+    c.cand_capacity = int(over.pop("cand_capacity", 4096 * max_events + 4096))
+    c.hit_capacity = int(over.pop("hit_capacity", 64 * max_hits + 4096))
+    v = h.get("vertex")
+    if v:
+        c.vertex_bins, c.vertex_threshold = int(v["n_bins"]), int(v["threshold"])
+        c.vertex_min_votes = int(v.get("min_track_votes", 0))
+        c.vertex_range = float(v["range"])
+        c.max_vertices = int(over.pop("max_vertices", v.get("max_vertices", 1024)))
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c
+
+
+class Hough2D:
+    """One trk2d handle (per-hit straight-line or interaction-point curved Hough)."""
+
+    def __init__(self, cfg: dict, max_events: int, max_hits: int, device: int = 0, **over):
+        self.lib = load_library()
+        self.cfg = hough2d_config(cfg, max_events, max_hits, **over)
+        h = C.c_void_p()
+        rc = self.lib.trk2d_create(C.byref(h), C.byref(self.cfg), device)
+        if rc != TRK_OK:
+            raise TrkError(rc, self.lib.trk2d_last_error(None).decode())
+        self.h = h
+        self.out = trk2d_result()
+
+    def reconstruct_device(self, hits, offsets, stream=None) -> int:
+        """hits: cuda float32 (N, 4); offsets: cuda int64 (n_events + 1).  Synchronises."""
+        return self.lib.trk2d_reconstruct(self.h, C.c_void_p(hits.data_ptr()), hits.shape[0],
+                                          C.c_void_p(offsets.data_ptr()), offsets.numel() - 1,
+                                          C.byref(self.out), C.c_void_p(_stream_handle(stream)))
+
+    def result(self, rc: int = TRK_OK):
+        """(candidates CAND2D_DTYPE, hit ids int32, cand_off int64) copied to the host."""
+        import torch
+        o = self.out
+        cand_off = np.ctypeslib.as_array(o.cand_off, shape=(o.n_events + 1,)).copy()
+        cand = torch.as_tensor(_DevArray(o.d_cand, (o.n_candidates * 32,), "|u1"), device="cuda") \
+            .cpu().numpy().view(CAND2D_DTYPE) if o.n_candidates else np.zeros(0, CAND2D_DTYPE)
+        hit_ids = torch.as_tensor(_DevArray(o.d_hit_ids, (o.n_hit_ids,), "<i4"), device="cuda") \
+            .cpu().numpy() if o.n_hit_ids else np.zeros(0, np.int32)
+        return cand, hit_ids, cand_off
+
+    def vertices(self):
+        """(vertices VERTEX_DTYPE, vertex_off int64, per vertex its candidate indices, overflow)
+        of the last call (vertex transform enabled)."""
+        import torch
+        o = self.out
+        if not o.vertex_off:
+            raise TrkError(TRK_ERR_INVALID, "the handle has no vertex transform")
+        voff = np.ctypeslib.as_array(o.vertex_off, shape=(o.n_events + 1,)).copy()
+        n = int(o.n_vertices)
+        v = torch.as_tensor(_DevArray(o.d_vertices, (n * 32,), "|u1"), device="cuda").cpu().numpy() \
+            .view(VERTEX_DTYPE) if n else np.zeros(0, VERTEX_DTYPE)
+        tracks = []
+        if n:
+            hi = int(v["track_off"].max()) + TRK2D_VERTEX_MAX_TRACKS
+            t = torch.as_tensor(_DevArray(o.d_vertex_tracks, (hi,), "<i4"), device="cuda").cpu().numpy()
+            tracks = [t[int(r["track_off"]):int(r["track_off"]) + int(r["n_tracks"])] for r in v]
+        return v, voff, tracks, int(o.vertex_overflow)
+
+    def histogram(self, event: int = 0):
+        import torch
+        out = torch.empty(self.cfg.n_cols * self.cfg.n_rows, dtype=torch.int32, device="cuda")
+        rc = self.lib.trk2d_get_histogram(self.h, event, C.c_void_p(out.data_ptr()), None)
+        if rc != TRK_OK:
+            raise TrkError(rc, self.error())
+        return out
+
+    def last_ms(self) -> dict:
+        a, b = C.c_float(0), C.c_float(0)
+        rc = self.lib.trk2d_last_ms(self.h, C.byref(a), C.byref(b))
+        if rc != TRK_OK:
+            raise TrkError(rc, self.error())
+        return {"vote_peak": a.value, "total": b.value}
+
+    def error(self) -> str:
+        return self.lib.trk2d_last_error(self.h).decode()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.trk2d_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

@@ -22,7 +22,7 @@ def lib_path():
 
 def declared_functions():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|int64_t|const char \*)\s*\*?\s*(trk_\w+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:int|void|int64_t|const char \*)\s*\*?\s*(trk(?:2d)?_\w+)\s*\(",
                                  text, re.M)))
 
 
@@ -36,7 +36,7 @@ def test_header_declares_the_boundary():
 def test_library_exports_every_declared_symbol(lib_path):
     out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
                          text=True, check=True).stdout
-    exported = set(re.findall(r"\b(trk_\w+)\b", out))
+    exported = set(re.findall(r"\b(trk(?:2d)?_\w+)\b", out))
     missing = [n for n in declared_functions() if n not in exported]
     assert not missing, missing
     lib = C.CDLL(lib_path)
@@ -60,10 +60,12 @@ def test_struct_layouts_match_c(tmp_path, lib_path):
 #define O(t, f) printf(#t "." #f " %zu\n", offsetof(t, f));
 int main(void) {
   S(trk_hit) S(trk_geometry) S(trk_binning) S(trk_options) S(trk_candidate) S(trk_candidates) S(trk_stats)
+  S(trk_track)
   O(trk_geometry, b_tesla) O(trk_geometry, triples) O(trk_binning, n) O(trk_binning, sagitta_fp64_cm)
   O(trk_options, vote_capacity) O(trk_options, tile_i) O(trk_options, use_graph)
   O(trk_candidate, hit_off) O(trk_candidate, params) O(trk_candidates, cand_off) O(trk_candidates, h_hit_ids)
-  O(trk_stats, ms_total)
+  O(trk_stats, ms_total) O(trk_options, fit_candidates) O(trk_candidates, d_tracks)
+  O(trk_candidates, h_hit_used) O(trk_track, chi2_rphi) O(trk_track, event) O(trk_track, layers)
   return 0; }
 ''')
     exe = tmp_path / "layout"
@@ -73,7 +75,8 @@ int main(void) {
     py = {"trk_hit": 16, "trk_geometry": C.sizeof(trk.trk_geometry),
           "trk_binning": C.sizeof(trk.trk_binning), "trk_options": C.sizeof(trk.trk_options),
           "trk_candidate": C.sizeof(trk.trk_candidate),
-          "trk_candidates": C.sizeof(trk.trk_candidates), "trk_stats": C.sizeof(trk.trk_stats)}
+          "trk_candidates": C.sizeof(trk.trk_candidates), "trk_stats": C.sizeof(trk.trk_stats),
+          "trk_track": C.sizeof(trk.trk_track)}
     for k, v in py.items():
         assert int(got[k]) == v, k
     for key, val in got.items():

@@ -1,0 +1,134 @@
+"""Pins of the 2-D per-hit Hough oracle (CPU only): straight lines (Sec. 7, Fig. 3) and
+curved tracks through the interaction point (Sec. 8, Fig. 5).
+
+  * exact points on a line / on a circle through the origin: at the true column every
+    hit's row value equals the true rho / q/pT (closed form), so all of them vote in one bin;
+  * the row value of a hit is the independent geometric quantity: the distance of the line
+    to the origin for rho, and 1/(K B R) of the circle through the origin, the hit and the
+    column's direction (checked against the circle built from its centre);
+  * the mirror wrap of the straight case: theta = 0 and pi are the same line with rho
+    negated (hand-built histogram), and the curved case wraps phi0;
+  * the peak rule on hand-built 2-D histograms, and a brute-force peak check.
+"""
+import numpy as np
+import pytest
+
+from oracle import hough2d as H
+
+K = 0.299792458e-2
+
+
+def _setup(kind, n_cols=64, n_rows=32, lo=-8.0, hi=8.0, T=3, b=0.0):
+    return H.Hough2DSetup(kind=kind, n_cols=n_cols, n_rows=n_rows, lo=lo, hi=hi, threshold=T,
+                          b_tesla=b)
+
+
+def test_straight_line_points_vote_in_one_bin():
+    s = _setup("straight", n_cols=180, n_rows=64, lo=-16.0, hi=16.0)
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        c = int(rng.integers(0, s.n_cols))
+        theta = s.columns()[c]
+        rho = rng.uniform(-15, 15)
+        t = rng.uniform(-100, 100, 10)
+        x = rho * np.cos(theta) - t * np.sin(theta)
+        y = rho * np.sin(theta) + t * np.cos(theta)
+        v = s.row_values(x, y)[:, c]
+        assert np.allclose(v, rho, atol=1e-12)
+        j, _ = H.votes(np.stack([x, y], 1), s)
+        assert len(set(j[:, c].tolist())) == 1
+
+
+def test_curved_ip_points_vote_in_one_bin():
+    B = 3.8
+    s = _setup("curved_ip", n_cols=256, n_rows=64, lo=-1.0, hi=1.0, b=B)
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        c = int(rng.integers(0, s.n_cols))
+        phi0 = s.columns()[c]
+        qopt = rng.uniform(-0.9, 0.9)
+        R = 1.0 / (K * B * abs(qopt))
+        sense = -np.sign(qopt)              # counter-clockwise (+) for negative charge
+        # circle through the origin leaving in direction phi0: centre at R along the normal
+        cx, cy = -sense * R * np.sin(phi0), sense * R * np.cos(phi0)
+        ang = np.arctan2(-cy, -cx) + sense * rng.uniform(0.01, 1.0, 10)
+        x, y = cx + R * np.cos(ang), cy + R * np.sin(ang)
+        v = s.row_values(x, y)[:, c]
+        assert np.allclose(v, qopt, rtol=1e-10, atol=1e-12)
+
+
+def test_curved_row_value_is_the_circle_through_origin_and_hit():
+    B = 2.0
+    s = _setup("curved_ip", n_cols=32, lo=-5.0, hi=5.0, b=B)
+    rng = np.random.default_rng(3)
+    x, y = rng.uniform(-50, 50, 20), rng.uniform(-50, 50, 20)
+    v = s.row_values(x, y)
+    for k in range(20):
+        for c, phi0 in enumerate(s.columns()):
+            # independent: centre on the normal to the direction at the origin, equidistant
+            # from the origin and the hit: c = t n, |t n - p|^2 = t^2 -> t = |p|^2 / (2 n.p)
+            n = np.array([-np.sin(phi0), np.cos(phi0)])
+            p = np.array([x[k], y[k]])
+            t = p @ p / (2 * (n @ p))
+            ccw = t > 0                       # centre on the left: counter-clockwise
+            qopt = (-1.0 if ccw else 1.0) / (K * B * abs(t))
+            assert np.isclose(v[k, c], qopt, rtol=1e-9)
+
+
+def test_straight_mirror_wrap_and_peak_rule():
+    s = _setup("straight", n_cols=8, n_rows=6, lo=-3.0, hi=3.0, T=2)
+    h = np.zeros(48, dtype=np.int64)
+    # (0, 1) = 5; its neighbour across the wrap is column 7, rows mirrored: 6-1-(1+dj)
+    h[0 * 6 + 1] = 5
+    h[7 * 6 + 4] = 5                       # mirror of row 1 in column 7: the same count
+    assert sorted(H.neighbours(0, 1, s)) == sorted([6 + 0, 6 + 1, 6 + 2, 0, 2,
+                                                    7 * 6 + 5, 7 * 6 + 4, 7 * 6 + 3])
+    # the tie goes to the smaller bin number: bin 1 is the peak, bin 46 is not
+    assert H.peaks(h, s).tolist() == [1]
+    h[7 * 6 + 4] = 6
+    assert H.peaks(h, s).tolist() == [46]
+    c = _setup("curved_ip", n_cols=8, n_rows=6, lo=-1.0, hi=1.0, T=2, b=1.0)
+    assert sorted(H.neighbours(0, 0, c)) == sorted([7 * 6 + 0, 7 * 6 + 1, 1, 6, 7])
+
+
+def test_peaks_brute_force():
+    rng = np.random.default_rng(4)
+    for kind in ("straight", "curved_ip"):
+        s = _setup(kind, n_cols=12, n_rows=9, lo=-1.0, hi=1.0, T=2, b=1.0)
+        for _ in range(100):
+            h = rng.integers(0, 5, s.n_cols * s.n_rows)
+            got = H.peaks(h, s).tolist()
+            want = []
+            for b in range(len(h)):
+                if h[b] < s.threshold:
+                    continue
+                c, j = divmod(b, s.n_rows)
+                nb = []
+                for dc in (-1, 0, 1):
+                    for dj in (-1, 0, 1):
+                        if dc == dj == 0:
+                            continue
+                        cc = c + dc
+                        jj = j + dj
+                        if not 0 <= cc < s.n_cols:
+                            cc %= s.n_cols
+                            if kind == "straight":
+                                jj = s.n_rows - 1 - jj
+                        if 0 <= jj < s.n_rows:
+                            nb.append(cc * s.n_rows + jj)
+                if all(h[b] >= h[n] for n in nb) and all(h[b] > h[n] for n in nb if n < b):
+                    want.append(b)
+            assert got == want
+
+
+def test_votes_and_hits_consistent():
+    s = _setup("curved_ip", n_cols=128, n_rows=32, lo=-1.0, hi=1.0, T=3, b=3.8)
+    rng = np.random.default_rng(5)
+    xy = rng.uniform(-100, 100, (300, 2))
+    ev = H.reconstruct(xy, np.array([0, 150, 300]), s)
+    for e, (a, b) in enumerate([(0, 150), (150, 300)]):
+        hh = ev[e]["hist"]
+        j, _ = H.votes(xy[a:b], s)
+        assert hh.sum() == (j >= 0).sum()
+        for bb, hits in zip(ev[e]["cand_bins"], ev[e]["cand_hits"]):
+            assert len(hits) == hh[bb] and np.all((hits >= a) & (hits < b))
