@@ -55,6 +55,9 @@ def parse():
                    help="skip the batched / plain-on-batch / served measurements")
     p.add_argument("--batch-events", type=int, default=256)
     p.add_argument("--serve-seconds", type=float, default=12.0)
+    p.add_argument("--hough2d", default=None, metavar="WORKLOAD",
+                   help="only time a per-hit 2-D Hough workload (sht_toy50, curved_ip200, "
+                        "sht_jets) and print its line")
     p.add_argument("--with-fit", action="store_true",
                    help="also fit a helix to every candidate inside each timed call")
     p.add_argument("--tuning", default=None, metavar="TI,TJ,LEVEL",
@@ -233,6 +236,16 @@ def main():
     if args.impl == "reference":
         run_reference(args, cfg, batch, rank, world)
         return
+    if args.hough2d:
+        import torch
+        torch.cuda.set_device(local)
+        from paper_1305_4855_gb300 import build
+        build.build()
+        line = {"metric": "events/s", "workload": args.hough2d, "n_gpus": 1,
+                **run_hough2d(args.hough2d, local, reps=max(args.steps, 1))}
+        line["value"] = line["events_per_s"]
+        print(json.dumps(line), flush=True)
+        return
 
     import torch
     torch.cuda.set_device(local)
@@ -358,7 +371,7 @@ def run_variants(args, local):
     batch = ev.make_batch(cfg, n_events=args.batch_events)
     n_trip = int(ev.layer_triplet_count(batch, cfg["geometry"]["triples"]).sum())
     out = {"candidate_fit": run_fit(args, local),
-           "hough2d": {w: run_hough2d(w, local) for w in ("sht_toy50", "curved_ip200")}}
+           "hough2d": {w: run_hough2d(w, local) for w in ("sht_toy50", "curved_ip200", "sht_jets")}}
     # --- batched: sub-batches of SUB events, each one trk_reconstruct (one graph launch)
     sub = 32
     per_event_max = int(np.diff(batch.offsets).max())
@@ -478,13 +491,17 @@ def run_hough2d(workload, local, reps=5):
             tot.append(ms["total"])
             vp.append(ms["vote_peak"])
     n_cand = int(h2.out.n_candidates)
+    n_vtx = int(h2.out.n_vertices)
     h2.close()
     t, v = float(np.mean(tot)), float(np.mean(vp))
     votes = batch.n_hits * cfg["hough2d"]["n_cols"]
-    return {"events": batch.n_events, "hits": batch.n_hits, "candidates": n_cand,
-            "call_ms": t, "events_per_s": batch.n_events / (t / 1000.0),
-            "vote_peak_ms": v, "hit_columns_per_s": votes / (v / 1000.0),
-            "l2": "flushed before each call (512 MB write)"}
+    out = {"events": batch.n_events, "hits": batch.n_hits, "candidates": n_cand,
+           "call_ms": t, "events_per_s": batch.n_events / (t / 1000.0),
+           "vote_peak_ms": v, "hit_columns_per_s": votes / (v / 1000.0),
+           "l2": "flushed before each call (512 MB write)"}
+    if "vertex" in cfg["hough2d"]:
+        out["vertices"] = n_vtx
+    return out
 
 
 def run_served(args, cfg, batch, capacity, local):

@@ -358,9 +358,9 @@ int trk_find_peaks_noalloc(const int32_t *hist, int32_t n_events, const trk_binn
  * candidate's hits are the hits that voted in its bin.  Hits use only x and y; layer and z
  * are ignored.  FP32 on the device.
  *
- * Vertices (TRK2D_STRAIGHT only, vertex_bins > 0) -- the paper's new trigger capability for
- * displaced jets: the track peaks of a jet lie on one sinusoid of (theta, rho), the sinusoid
- * of the jet's vertex, and a second Hough transform over the peaks finds it.  Each candidate
+ * Vertices (TRK2D_STRAIGHT only, vertex_bins > 0) -- Sec. 9 and Figs. 7-8, displaced jets:
+ * the track peaks of a jet lie on one sinusoid of (theta, rho), the sinusoid of the jet's
+ * vertex, and a second Hough transform over the peaks finds it.  Each candidate
  * with votes >= vertex_min_votes draws its line x cos(theta) + y sin(theta) = rho (bin
  * centres, FP64) into a vertex_bins x vertex_bins grid over [-vertex_range, vertex_range)^2
  * (cell centres g_a = -range + (a + 1/2) w): once per x column in the row of
@@ -397,7 +397,8 @@ typedef struct trk2d_vertex {               /* 32 bytes */
     uint32_t cell;                          /* a * vertex_bins + b */
     int32_t event;
     int32_t votes;                          /* candidate lines through the cell */
-    int32_t n_tracks;                       /* listed: min(votes, TRK2D_VERTEX_MAX_TRACKS) */
+    int32_t n_tracks;                       /* listed: min(votes, TRK2D_VERTEX_MAX_TRACKS),
+                                               the candidates with the smallest indices */
     float xy[2];                            /* cell centre (cm) */
     int64_t track_off;                      /* its tracks: vertex_tracks[track_off ..
                                                track_off + n_tracks), candidate indices into
@@ -443,6 +444,14 @@ int trk2d_create(trk2d_ctx **out, const trk2d_config *config, int32_t device);
 int trk2d_reconstruct(trk2d_ctx *h, const trk_hit *hits, int64_t n_hits,
                       const int64_t *event_offsets, int32_t n_events, trk2d_result *out,
                       void *stream);
+
+/* The vertex transform alone, over candidates the caller supplies (DEVICE arrays: cand
+ * sorted by event, cand_off [n_events + 1] the per-event ranges; only bin, event and votes
+ * are read): for peaks found elsewhere.  Needs a handle created with vertex_bins.  Fills
+ * the vertex fields of out (the candidate fields are zero); vertex track indices point
+ * into the caller's cand.  Synchronous. */
+int trk2d_find_vertices(trk2d_ctx *h, const trk2d_candidate *cand, const int64_t *cand_off,
+                        int32_t n_events, trk2d_result *out, void *stream);
 
 /* Copy event e's histogram of the last call (n_cols x n_rows int32, DEVICE dst).
  * Synchronous. */

@@ -162,9 +162,9 @@ def reconstruct(xy: np.ndarray, offsets: np.ndarray, s: Hough2DSetup) -> list:
 
 
 # ---------------------------------------------------------------------------------------
-# Second transform: displaced-jet vertices (the paper's "new trigger capabilities": the
-# track peaks of a displaced jet lie on one sinusoid of the (theta, rho) space, the
-# sinusoid of the jet's vertex, and a second Hough transform over the peaks finds it).
+# Second transform: displaced-jet vertices (Sec. 9 and Figs. 7-8: the track peaks of a
+# displaced jet lie on one sinusoid of the (theta, rho) space, the sinusoid of the jet's
+# vertex, and a second Hough transform over the peaks finds it).
 # Reading: a vertex (xv, yv) lies on every track line x cos(theta) + y sin(theta) = rho of
 # its jet, so each straight-line candidate votes along its line in a binned (xv, yv)
 # space: n_bins x n_bins cells over [-range, range)^2, cell centres g_a = -range + (a + 1/2) w.

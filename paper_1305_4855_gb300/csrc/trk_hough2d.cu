@@ -246,24 +246,55 @@ __global__ void k_h2_cand_off(const uint32_t *wprefix, int64_t W, int n_events,
 
 constexpr int kVtxThreads = 256;
 
-// Cell of the line of candidate bin `bin` at step a (column or row), or -1.
-__device__ __forceinline__ int vtx_cell(const H2Const &K, uint32_t bin, int a)
+// Line geometry of a candidate, computed once (FP64): cos and sin of its theta and rho.
+struct VtxLine {
+    double c, s, rho;
+    int by_col;      // sweep x columns (|sin| >= |cos|) or y rows
+    int pad;
+};
+
+__global__ void k_h2_cand_geom(H2Const K, const trk2d_candidate *cand,
+                               const unsigned long long *n_dev, int64_t n_host, int64_t cap,
+                               VtxLine *geom)
 {
-    const int col = (int)(bin / (uint32_t)K.n_rows), row = (int)(bin % (uint32_t)K.n_rows);
-    const double theta = K.col_lo_d + (col + 0.5) * K.col_w_d;
-    const double rho = K.lo_d + (row + 0.5) * K.w_d;
-    const double c = cos(theta), s = sin(theta);
+    int64_t n = n_dev ? (int64_t)*n_dev : n_host;
+    n = n < cap ? n : cap;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t bin = cand[i].bin;
+        const int col = (int)(bin / (uint32_t)K.n_rows), row = (int)(bin % (uint32_t)K.n_rows);
+        const double theta = K.col_lo_d + (col + 0.5) * K.col_w_d;
+        VtxLine L;
+        sincos(theta, &L.s, &L.c);
+        L.rho = K.lo_d + (row + 0.5) * K.w_d;
+        L.by_col = fabs(L.s) >= fabs(L.c);
+        L.pad = 0;
+        geom[i] = L;
+    }
+}
+
+// Cell of a line at step a (its swept column or row), or -1.
+__device__ __forceinline__ int vtx_cell(const H2Const &K, const VtxLine &L, int a)
+{
     const double g = -K.v_range + (a + 0.5) * K.v_w;
-    const bool by_col = fabs(s) >= fabs(c);
-    const double other = by_col ? (rho - g * c) / s : (rho - g * s) / c;
+    const double other = L.by_col ? (L.rho - g * L.c) / L.s : (L.rho - g * L.s) / L.c;
     if (!(other >= -K.v_range && other < K.v_range))
         return -1;
     int k = (int)floor((other + K.v_range) / K.v_w);
     k = k >= K.vb ? K.vb - 1 : k;
-    return by_col ? a * K.vb + k : k * K.vb + a;
+    return L.by_col ? a * K.vb + k : k * K.vb + a;
+}
+
+// Does the raster of candidate bin `bin` contain `cell`?  (It visits one cell per swept
+// column or row, so only the step through the cell's column or row is evaluated.)
+__device__ __forceinline__ bool vtx_raster_has(const H2Const &K, const VtxLine &L, int cell)
+{
+    const int a = cell / K.vb, b = cell - (cell / K.vb) * K.vb;
+    return vtx_cell(K, L, L.by_col ? a : b) == cell;
 }
 
 __global__ void __launch_bounds__(kVtxThreads) k_h2_vertex(H2Const K, const trk2d_candidate *cand,
+                                                           const VtxLine *geom,
                                                            const int64_t *cand_off,
                                                            int64_t cand_cap,
                                                            trk2d_vertex *slots,
@@ -285,10 +316,10 @@ __global__ void __launch_bounds__(kVtxThreads) k_h2_vertex(H2Const K, const trk2
         s_ntr[q] = 0;
     __syncthreads();
     for (int64_t q = threadIdx.x; q < nc * nb; q += kVtxThreads) {
-        const trk2d_candidate cd = cand[c0 + q / nb];
-        if (cd.votes < K.v_min_votes)
+        const int64_t i = c0 + q / nb;
+        if (cand[i].votes < K.v_min_votes)
             continue;
-        const int cell = vtx_cell(K, cd.bin, (int)(q % nb));
+        const int cell = vtx_cell(K, geom[i], (int)(q % nb));
         if (cell >= 0)
             atomicAdd(&vh[cell], 1);
     }
@@ -378,17 +409,44 @@ __global__ void __launch_bounds__(kVtxThreads) k_h2_vertex(H2Const K, const trk2
         vh[slots[(size_t)e * K.max_vertices + k].cell] = -(k + 1);
     __syncthreads();
     for (int64_t q = threadIdx.x; q < nc * nb; q += kVtxThreads) {
-        const trk2d_candidate cd = cand[c0 + q / nb];
-        if (cd.votes < K.v_min_votes)
+        const int64_t i = c0 + q / nb;
+        if (cand[i].votes < K.v_min_votes)
             continue;
-        const int cell = vtx_cell(K, cd.bin, (int)(q % nb));
+        const int cell = vtx_cell(K, geom[i], (int)(q % nb));
         if (cell < 0 || vh[cell] >= 0)
             continue;
         const int slot = -vh[cell] - 1;
+        if (slots[(size_t)e * K.max_vertices + slot].votes > TRK2D_VERTEX_MAX_TRACKS)
+            continue;                            // listed below, in candidate order
         const int k = atomicAdd(&s_ntr[slot], 1);
         if (k < TRK2D_VERTEX_MAX_TRACKS)
             slot_tracks[((int64_t)e * K.max_vertices + slot) * TRK2D_VERTEX_MAX_TRACKS + k] =
                 (int32_t)(c0 + q / nb);
+    }
+    __syncthreads();
+    // vertices with more lines than list entries: a warp walks the candidates in order and
+    // keeps the first TRK2D_VERTEX_MAX_TRACKS whose raster contains the cell
+    for (int k = w; k < nv; k += kVtxThreads / 32) {
+        const trk2d_vertex &v = slots[(size_t)e * K.max_vertices + k];
+        if (v.votes <= TRK2D_VERTEX_MAX_TRACKS)
+            continue;
+        int32_t *t = slot_tracks + ((int64_t)e * K.max_vertices + k) * TRK2D_VERTEX_MAX_TRACKS;
+        int n = 0;
+        for (int64_t i0 = 0; i0 < nc && n < TRK2D_VERTEX_MAX_TRACKS; i0 += 32) {
+            const int64_t i = i0 + lane;
+            bool has = false;
+            if (i < nc) {
+                has = cand[c0 + i].votes >= K.v_min_votes &&
+                      vtx_raster_has(K, geom[c0 + i], (int)v.cell);
+            }
+            const unsigned m = __ballot_sync(kFull, has);
+            const int at = n + __popc(m & lanemask_lt());
+            if (has && at < TRK2D_VERTEX_MAX_TRACKS)
+                t[at] = (int32_t)(c0 + i);
+            n += __popc(m);
+        }
+        if (lane == 0)
+            s_ntr[k] = n < TRK2D_VERTEX_MAX_TRACKS ? n : TRK2D_VERTEX_MAX_TRACKS;
     }
     __syncthreads();
     // ascending track lists (one thread per vertex: at most 64 entries)
@@ -457,6 +515,8 @@ struct trk2d_ctx {
     H2Counters *d_ctr = nullptr, *h_ctr = nullptr;
     int64_t *h_cand_off = nullptr;
     trk2d_vertex *d_vslots = nullptr, *d_vertices = nullptr;
+    VtxLine *d_geom = nullptr;
+    int64_t geom_cap = 0;
     int32_t *d_vtracks = nullptr, *d_vcount = nullptr, *d_voverflow = nullptr;
     int64_t *d_voff = nullptr, *h_voff = nullptr;
     int32_t h_voverflow = 0;
@@ -488,7 +548,7 @@ void free2(trk2d_ctx *h)
     void *dev[] = {h->d_coef,    h->d_hist,     h->d_cbits,    h->d_wprefix,  h->d_bsum,
                    h->d_hit_off, h->d_cand_off, h->d_cand,     h->d_hit_ids,  h->d_ctr,
                    h->d_vslots,  h->d_vertices, h->d_vtracks,  h->d_vcount,   h->d_voverflow,
-                   h->d_voff};
+                   h->d_voff,    h->d_geom};
     for (void *p : dev)
         if (p)
             cudaFree(p);
@@ -520,6 +580,42 @@ cudaError_t dalloc2(T **p, size_t n)
         if (e_ != cudaSuccess)                                                                 \
             return fail2(h, TRK_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
+
+// The vertex stage over candidates cand (cand_off[e] .. cand_off[e + 1] per event): the
+// kernel, the per-event counts' scan, the dense copy, and the copies of the offsets and the
+// overflow flag to the host.
+static int enqueue_vertices(trk2d_ctx *h, const trk2d_candidate *cand, const int64_t *cand_off,
+                            const unsigned long long *n_cand_dev, int64_t cand_cap, int n_events,
+                            cudaStream_t s)
+{
+    const H2Const &K = h->K;
+    if (cand_cap > h->geom_cap) {           // only the standalone entry can need more
+        if (h->d_geom)
+            cudaFree(h->d_geom);
+        h->d_geom = nullptr;
+        h->geom_cap = 0;
+        H2_CUDA(h, dalloc2(&h->d_geom, (size_t)cand_cap));
+        h->geom_cap = cand_cap;
+    }
+    H2_CUDA(h, cudaMemsetAsync(h->d_voverflow, 0, sizeof(int32_t), s));
+    k_h2_cand_geom<<<h->n_sm * 4, 256, 0, s>>>(K, cand, n_cand_dev, cand_cap, cand_cap, h->d_geom);
+    H2_CUDA(h, cudaGetLastError());
+    k_h2_vertex<<<n_events, kVtxThreads, sizeof(int32_t) * K.vb * K.vb, s>>>(
+        K, cand, h->d_geom, cand_off, cand_cap, h->d_vslots, h->d_vtracks, h->d_vcount,
+        h->d_voverflow);
+    H2_CUDA(h, cudaGetLastError());
+    H2_CUDA(h, scan_exclusive(CountVal{h->d_vcount}, nullptr, n_events, n_events, h->d_voff,
+                              h->d_bsum, nullptr, s));
+    k_h2_vertex_total<<<1, 32, 0, s>>>(h->d_voff, h->d_vcount, n_events, h->d_voff);
+    k_h2_vertex_pack<<<h->n_sm * 2, 256, 0, s>>>(h->d_vslots, h->d_vcount, h->d_voff, n_events,
+                                                 K.max_vertices, h->d_vertices);
+    H2_CUDA(h, cudaGetLastError());
+    H2_CUDA(h, cudaMemcpyAsync(h->h_voff, h->d_voff, sizeof(int64_t) * (n_events + 1),
+                               cudaMemcpyDeviceToHost, s));
+    H2_CUDA(h, cudaMemcpyAsync(&h->h_voverflow, h->d_voverflow, sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, s));
+    return TRK_OK;
+}
 
 extern "C" int trk2d_create(trk2d_ctx **out, const trk2d_config *c, int32_t device)
 {
@@ -635,7 +731,9 @@ extern "C" int trk2d_create(trk2d_ctx **out, const trk2d_config *c, int32_t devi
              dalloc2(&h->d_vcount, (size_t)E) == cudaSuccess &&
              dalloc2(&h->d_voverflow, 1) == cudaSuccess &&
              dalloc2(&h->d_voff, (size_t)E + 1) == cudaSuccess &&
+             dalloc2(&h->d_geom, (size_t)c->cand_capacity) == cudaSuccess &&
              cudaMallocHost((void **)&h->h_voff, sizeof(int64_t) * (size_t)(E + 1)) == cudaSuccess &&
+             (h->geom_cap = c->cand_capacity) > 0 &&
              cudaFuncSetAttribute(k_h2_vertex, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(sizeof(int32_t) * c->vertex_bins * c->vertex_bins)) ==
                  cudaSuccess;
@@ -696,21 +794,10 @@ extern "C" int trk2d_reconstruct(trk2d_ctx *h, const trk_hit *hits, int64_t n_hi
                                                              &ctr->n_cand, h->d_cand_off);
     H2_CUDA(h, cudaGetLastError());
     if (K.vb > 0) {
-        H2_CUDA(h, cudaMemsetAsync(h->d_voverflow, 0, sizeof(int32_t), s));
-        k_h2_vertex<<<n_events, kVtxThreads, sizeof(int32_t) * K.vb * K.vb, s>>>(
-            K, h->d_cand, h->d_cand_off, h->cfg.cand_capacity, h->d_vslots, h->d_vtracks,
-            h->d_vcount, h->d_voverflow);
-        H2_CUDA(h, cudaGetLastError());
-        H2_CUDA(h, scan_exclusive(CountVal{h->d_vcount}, nullptr, n_events, n_events, h->d_voff,
-                                  h->d_bsum, nullptr, s));
-        k_h2_vertex_total<<<1, 32, 0, s>>>(h->d_voff, h->d_vcount, n_events, h->d_voff);
-        k_h2_vertex_pack<<<h->n_sm * 2, 256, 0, s>>>(h->d_vslots, h->d_vcount, h->d_voff,
-                                                     n_events, K.max_vertices, h->d_vertices);
-        H2_CUDA(h, cudaGetLastError());
-        H2_CUDA(h, cudaMemcpyAsync(h->h_voff, h->d_voff, sizeof(int64_t) * (n_events + 1),
-                                   cudaMemcpyDeviceToHost, s));
-        H2_CUDA(h, cudaMemcpyAsync(&h->h_voverflow, h->d_voverflow, sizeof(int32_t),
-                                   cudaMemcpyDeviceToHost, s));
+        const int rc = enqueue_vertices(h, h->d_cand, h->d_cand_off, &h->d_ctr->n_cand,
+                                        h->cfg.cand_capacity, n_events, s);
+        if (rc != TRK_OK)
+            return rc;
     }
     H2_CUDA(h, cudaMemcpyAsync(h->h_ctr, ctr, sizeof(H2Counters), cudaMemcpyDeviceToHost, s));
     H2_CUDA(h, cudaMemcpyAsync(h->h_cand_off, h->d_cand_off, sizeof(int64_t) * (n_events + 1),
@@ -735,6 +822,40 @@ extern "C" int trk2d_reconstruct(trk2d_ctx *h, const trk_hit *hits, int64_t n_hi
     }
     if (over)
         return fail2(h, TRK_ERR_CAPACITY, "candidate or hit capacity exceeded");
+    return TRK_OK;
+}
+
+extern "C" int trk2d_find_vertices(trk2d_ctx *h, const trk2d_candidate *cand,
+                                   const int64_t *cand_off, int32_t n_events, trk2d_result *out,
+                                   void *stream)
+{
+    if (!h)
+        return TRK_ERR_INVALID;
+    if (h->K.vb <= 0)
+        return fail2(h, TRK_ERR_INVALID, "the handle was created without vertex_bins");
+    if (!cand || !cand_off || n_events < 1 || n_events > h->cfg.max_events)
+        return fail2(h, TRK_ERR_INVALID, "bad arguments (null pointer or event count)");
+    H2_CUDA(h, cudaSetDevice(h->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->own;
+    int64_t last = 0;
+    H2_CUDA(h, cudaMemcpyAsync(&last, cand_off + n_events, sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, s));
+    H2_CUDA(h, cudaStreamSynchronize(s));
+    if (last < 0)
+        return fail2(h, TRK_ERR_INVALID, "bad candidate offsets");
+    const int rc = enqueue_vertices(h, cand, cand_off, nullptr, last, n_events, s);
+    if (rc != TRK_OK)
+        return rc;
+    H2_CUDA(h, cudaStreamSynchronize(s));
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        out->n_events = n_events;
+        out->n_vertices = h->h_voff[n_events];
+        out->vertex_off = h->h_voff;
+        out->d_vertices = h->d_vertices;
+        out->d_vertex_tracks = h->d_vtracks;
+        out->vertex_overflow = h->h_voverflow;
+    }
     return TRK_OK;
 }
 

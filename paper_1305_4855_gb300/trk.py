@@ -30,7 +30,7 @@ EXPORTED = ["trk_options_default", "trk_create", "trk_reconstruct", "trk_reconst
             "trk_find_peaks_noalloc", "trk_server_create", "trk_server_submit", "trk_server_wait",
             "trk_server_take", "trk_server_counts", "trk_server_destroy",
             "trk2d_create", "trk2d_reconstruct", "trk2d_get_histogram", "trk2d_last_ms",
-            "trk2d_last_error", "trk2d_destroy"]
+            "trk2d_last_error", "trk2d_destroy", "trk2d_find_vertices"]
 TRK2D_STRAIGHT, TRK2D_CURVED_IP = 0, 1
 
 
@@ -205,6 +205,8 @@ def load_library(path: str = LIB_PATH):
     lib.trk2d_last_error.restype = C.c_char_p
     lib.trk2d_destroy.argtypes = [vp]
     lib.trk2d_destroy.restype = C.c_int
+    lib.trk2d_find_vertices.argtypes = [vp, vp, vp, i32, vp, vp]
+    lib.trk2d_find_vertices.restype = C.c_int
     _lib = lib
     return lib
 
@@ -602,6 +604,17 @@ class Hough2D:
             t = torch.as_tensor(_DevArray(o.d_vertex_tracks, (hi,), "<i4"), device="cuda").cpu().numpy()
             tracks = [t[int(r["track_off"]):int(r["track_off"]) + int(r["n_tracks"])] for r in v]
         return v, voff, tracks, int(o.vertex_overflow)
+
+    def find_vertices(self, cand: np.ndarray, cand_off: np.ndarray, stream=None) -> int:
+        """The vertex transform over given candidates (CAND2D_DTYPE host array sorted by
+        event, int64 offsets); results through vertices()."""
+        import torch
+        c = torch.from_numpy(np.ascontiguousarray(cand).view(np.uint8).copy()).cuda()
+        o = torch.from_numpy(np.ascontiguousarray(cand_off, dtype=np.int64)).cuda()
+        self._keep = (c, o)
+        return self.lib.trk2d_find_vertices(self.h, C.c_void_p(c.data_ptr()), C.c_void_p(o.data_ptr()),
+                                            len(cand_off) - 1, C.byref(self.out),
+                                            C.c_void_p(_stream_handle(stream)))
 
     def histogram(self, event: int = 0):
         import torch

@@ -109,3 +109,83 @@ def test_rejects_bad_configs(trk):
     bad = dict(cfg, hough2d=dict(cfg["hough2d"], n_cols=2))
     with pytest.raises(trk.TrkError):
         trk.Hough2D(bad, max_events=1, max_hits=10)
+
+
+def test_vertex_transform_parity(trk):
+    """Displaced jets: the second transform over the oracle's own straight-line candidates
+    (fed to trk2d_find_vertices) against the oracle's vertex transform of the same
+    candidates: vertices, votes and track lists equal away from oracle-flagged cells."""
+    cfg = ev.load_workload("sht_jets")
+    b = ev.make_batch(cfg, n_events=6)
+    s = H.Hough2DSetup.from_workload(cfg)
+    vs = H.VertexSetup.from_workload(cfg)
+    ref = H.reconstruct(b.xyz[:, :2].astype(np.float64), b.offsets, s)
+    cand = np.zeros(sum(len(e["cand_bins"]) for e in ref), dtype=trk.CAND2D_DTYPE)
+    off = np.zeros(b.n_events + 1, dtype=np.int64)
+    k = 0
+    for e, oe in enumerate(ref):
+        n = len(oe["cand_bins"])
+        cand["bin"][k:k + n] = oe["cand_bins"]
+        cand["event"][k:k + n] = e
+        cand["votes"][k:k + n] = oe["cand_votes"]
+        k += n
+        off[e + 1] = k
+    h2 = trk.Hough2D(cfg, max_events=b.n_events, max_hits=b.n_hits)
+    rc = h2.find_vertices(cand, off)
+    assert rc == 0, h2.error()
+    verts, voff, vtracks, over = h2.vertices()
+    h2.close()
+    assert over == 0
+    n_vtx = n_skip = found = 0
+    for e, oe in enumerate(ref):
+        ge = verts[int(voff[e]):int(voff[e + 1])]
+        assert np.all(np.diff(ge["cell"].astype(np.int64)) > 0) and np.all(ge["event"] == e)
+        ov = H.event_vertices(oe, vs)
+        aff = set()
+        for c in ov["amb_cells"]:
+            aff.add(c)
+            aff.update(H.vertex_neighbours(c, vs))
+        gmap = {int(v["cell"]): i for i, v in enumerate(ge)}
+        omap = {int(c): i for i, c in enumerate(ov["cells"])}
+        for c in set(gmap) ^ set(omap):
+            assert c in aff, (e, c)
+        for c in set(gmap) & set(omap):
+            if c in aff:
+                n_skip += 1
+                continue
+            g, o = ge[gmap[c]], omap[c]
+            assert g["votes"] == ov["votes"][o]
+            gt = vtracks[int(voff[e]) + gmap[c]] - int(off[e])
+            assert np.array_equal(gt, ov["tracks"][o][:64]), (e, c)
+            assert np.array_equal(g["xy"], ov["centres"][o].astype(np.float32))
+            n_vtx += 1
+        tv = b.extra["vertices"][b.extra["vertices"][:, 3] == e]
+        for x, y, *_ in tv:
+            if len(ge):
+                found += np.hypot(ge["xy"][:, 0] - x, ge["xy"][:, 1] - y).min() < 2.5
+    print("VTX", dict(vertices_compared=n_vtx, skipped_flagged=n_skip, true_found=int(found),
+                      true=len(b.extra["vertices"])))
+    assert n_vtx > 100
+
+
+def test_vertex_end_to_end_properties(trk):
+    """The whole chain (first transform, candidates, second transform) in one call:
+    vertices sorted per event, votes above the threshold, track lists ascending and made of
+    candidates with enough votes."""
+    cfg = ev.load_workload("sht_jets")
+    b = ev.make_batch(cfg, n_events=16)
+    vs = H.VertexSetup.from_workload(cfg)
+    h2 = trk.Hough2D(cfg, max_events=b.n_events, max_hits=b.n_hits)
+    rc = h2.reconstruct_device(torch.from_numpy(b.packed()).cuda(), torch.from_numpy(b.offsets).cuda())
+    assert rc == 0, h2.error()
+    cand, hit_ids, cand_off = h2.result(rc)
+    verts, voff, vtracks, over = h2.vertices()
+    h2.close()
+    assert len(verts) > 0 and voff[-1] == len(verts)
+    for e in range(b.n_events):
+        ge = verts[int(voff[e]):int(voff[e + 1])]
+        assert np.all(np.diff(ge["cell"].astype(np.int64)) > 0)
+        assert np.all(ge["votes"] >= vs.threshold)
+    for v, t in zip(verts, vtracks):
+        assert len(t) == min(int(v["votes"]), 64) and np.all(np.diff(t) > 0)
+        assert np.all(cand["votes"][t] >= vs.min_track_votes) and np.all(cand["event"][t] == v["event"])

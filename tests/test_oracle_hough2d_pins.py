@@ -132,3 +132,51 @@ def test_votes_and_hits_consistent():
         assert hh.sum() == (j >= 0).sum()
         for bb, hits in zip(ev[e]["cand_bins"], ev[e]["cand_hits"]):
             assert len(hits) == hh[bb] and np.all((hits >= a) & (hits < b))
+
+
+# ---------------------------------------------------------------------------------------
+# the second transform (displaced-jet vertices)
+# ---------------------------------------------------------------------------------------
+
+def test_lines_through_a_point_meet_in_its_cell():
+    vs = H.VertexSetup(n_bins=64, range=64.0, threshold=3)
+    rng = np.random.default_rng(6)
+    w = 2 * vs.range / vs.n_bins
+    for _ in range(30):
+        x0, y0 = rng.uniform(-60, 60, 2)
+        thetas = rng.uniform(0, np.pi, 8)
+        rhos = x0 * np.cos(thetas) + y0 * np.sin(thetas)
+        r = H.vertex_hough(np.stack([thetas, rhos], 1), vs)
+        cell = int(np.floor((x0 + vs.range) / w)) * vs.n_bins + int(np.floor((y0 + vs.range) / w))
+        # each line passes through the vertex; its raster may take the neighbouring cell of
+        # the swept column or row, never farther
+        a0, b0 = divmod(cell, vs.n_bins)
+        near = [i for i in range(vs.n_bins ** 2)
+                if abs(i // vs.n_bins - a0) <= 1 and abs(i % vs.n_bins - b0) <= 1]
+        assert r["hist"][near].sum() >= 8
+        assert any(abs(c // vs.n_bins - a0) <= 1 and abs(c % vs.n_bins - b0) <= 1
+                   for c in r["cells"])
+
+
+def test_line_raster_one_vote_per_step():
+    vs = H.VertexSetup(n_bins=32, range=10.0, threshold=1)
+    for theta in (0.1, 0.7, np.pi / 4, 1.2, np.pi / 2, 2.5, 3.0):
+        votes = H.vertex_votes(np.array([[theta, 1.5]]), vs)[0]
+        by_col = abs(np.sin(theta)) >= abs(np.cos(theta))
+        steps = [a for (_, _, bc, a, _) in votes]
+        assert len(steps) == len(set(steps)) and all(bc == by_col for (_, _, bc, _, _) in votes)
+        # the raster is connected: consecutive steps move at most one cell across
+        ks = [k for (*_, k) in votes]
+        assert all(abs(k1 - k0) <= 1 for k0, k1 in zip(ks, ks[1:]))
+        # every voted cell centre lies within half a diagonal of the line
+        w = 2 * vs.range / vs.n_bins
+        for cell, *_ in votes:
+            a, b = divmod(cell, vs.n_bins)
+            xc, yc = -vs.range + (a + 0.5) * w, -vs.range + (b + 0.5) * w
+            assert abs(xc * np.cos(theta) + yc * np.sin(theta) - 1.5) <= w * 0.75
+
+
+def test_vertex_peak_rule_no_wrap():
+    vs = H.VertexSetup(n_bins=5, range=5.0, threshold=2)
+    assert sorted(H.vertex_neighbours(0, vs)) == [1, 5, 6]
+    assert len(H.vertex_neighbours(12, vs)) == 8
