@@ -597,30 +597,36 @@ __global__ void __launch_bounds__(kAssignThreads, 1) k_assign_fill(AssignArgs A)
     const int64_t n_slots = n_chunks * kWarp;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // Only ~1 % of the votes land in candidate bins, so the kernel is a stream over the
-    // vote list.  Each thread takes kU vote slots a grid stride apart (a warp covers whole
-    // 32-slot chunks) and issues their vote, chunk count and chunk event loads together;
-    // votes are read once, with the streaming (evict-first) hint.  Slots past a chunk's
-    // count hold stale data and are discarded.  The shared-memory candidate filter then
-    // leaves the bitmap lookup (a random 32-byte L2 sector per vote) to the few votes
-    // whose filter bit is set.
-    constexpr int kU = 8;
-    for (int64_t s0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s0 < n_slots;
-         s0 += kU * stride) {
+    // vote list.  Each thread takes kP pairs of adjacent vote slots (one 16-byte load each,
+    // a warp covers two whole 32-slot chunks) a grid stride apart and issues their vote,
+    // chunk count and chunk event loads together; votes are read once, with the streaming
+    // (evict-first) hint.  Slots past a chunk's count hold stale data and are discarded.
+    // The shared-memory candidate filter then leaves the bitmap lookup (a random 32-byte
+    // L2 sector per vote) to the few votes whose filter bit is set.
+    constexpr int kP = 4, kU = 2 * kP;
+    const int64_t n_pairs = n_slots / 2;
+    for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p0 < n_pairs;
+         p0 += kP * stride) {
         uint64_t v[kU];
         int ev[kU];
         int cnt[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int64_t slot = s0 + u * stride;
-            const bool in = slot < n_slots;
-            v[u] = in ? __ldcs(reinterpret_cast<const unsigned long long *>(A.votes) + slot) : 0ull;
-            cnt[u] = in ? __ldg(A.chunk_count + (slot >> 5)) : 0;
-            ev[u] = in ? __ldg(A.chunk_event + (slot >> 5)) : 0;
+        for (int u = 0; u < kP; ++u) {
+            const int64_t pr = p0 + u * stride;
+            const bool in = pr < n_pairs;
+            const int64_t slot = 2 * pr;
+            ulonglong2 two = make_ulonglong2(0ull, 0ull);
+            if (in)
+                two = __ldcs(reinterpret_cast<const ulonglong2 *>(A.votes) + pr);
+            v[2 * u] = two.x;
+            v[2 * u + 1] = two.y;
+            cnt[2 * u] = cnt[2 * u + 1] = in ? __ldg(A.chunk_count + (slot >> 5)) : 0;
+            ev[2 * u] = ev[2 * u + 1] = in ? __ldg(A.chunk_event + (slot >> 5)) : 0;
         }
         uint32_t word[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            const int64_t slot = s0 + u * stride;
+            const int64_t slot = 2 * (p0 + (u >> 1) * stride) + (u & 1);
             const uint32_t bin = (uint32_t)v[u];
             if ((int)(slot & 31) >= cnt[u]) {
                 ev[u] = -1;
@@ -633,7 +639,7 @@ __global__ void __launch_bounds__(kAssignThreads, 1) k_assign_fill(AssignArgs A)
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            const int64_t slot = s0 + u * stride;
+            const int64_t slot = 2 * (p0 + (u >> 1) * stride) + (u & 1);
             const uint32_t bin = (uint32_t)v[u];
             if (ev[u] < 0 || !((word[u] >> (bin & 31)) & 1u))
                 continue;

@@ -104,6 +104,18 @@ def test_barrel10_reduced_event(trk):
     assert reps[0]["n_both"] > 10000
 
 
+@pytest.mark.parametrize("dims", [(15, 13, 9, 7, 5), (17, 32, 16, 16, 16)])
+def test_odd_binnings(trk, dims):
+    """Bin counts whose inner block (d0 x cot x z0) is odd and not a multiple of 4 (the
+    scalar peak pass), and a non-power-of-two phi0 count, on the reduced 10-layer event."""
+    cfg = ev.load_workload("barrel10_500trk")
+    cfg["events"]["n_tracks"] = 40
+    cfg["binning"]["n"] = list(dims)
+    cfg["binning"]["threshold"] = 3
+    reps = _full_compare(trk, cfg, ev.make_batch(cfg, seed=23))
+    assert reps[0]["n_both"] > 5000
+
+
 def test_batch_of_uneven_events(trk):
     cfg = ev.load_workload("barrel10_500trk")
     rng = np.random.default_rng(5)
