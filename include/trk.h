@@ -281,7 +281,8 @@ typedef struct trk_served_event {
     int64_t n_hit_ids;
 } trk_served_event;
 
-/* Create a server of n_lanes (1..16) lanes; each lane allocates one trk handle. */
+/* Create a server of n_lanes (1..16) lanes; each lane allocates one trk handle with
+ * lane_options (fit_candidates is ignored: served events return candidates and hits). */
 int trk_server_create(trk_server **out, const trk_geometry *geometry, const trk_binning *binning,
                       const trk_options *lane_options, int32_t n_lanes);
 
@@ -460,7 +461,8 @@ int trk2d_get_histogram(trk2d_ctx *h, int32_t event, int32_t *dst, void *stream)
 /* Device time (ms) of the last call's vote-and-peak kernel and of the whole call. */
 int trk2d_last_ms(trk2d_ctx *h, float *vote_peak_ms, float *total_ms);
 
-/* Text of the last error on a 2-D handle (NULL: of the last failed trk2d_create). */
+/* Text of the last error on a 2-D handle (NULL: of the calling thread's last failed
+ * trk2d_create). */
 const char *trk2d_last_error(const trk2d_ctx *h);
 
 int trk2d_destroy(trk2d_ctx *h);

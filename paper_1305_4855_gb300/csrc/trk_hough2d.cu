@@ -14,7 +14,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include <cuda_runtime.h>
@@ -293,6 +292,24 @@ __device__ __forceinline__ bool vtx_raster_has(const H2Const &K, const VtxLine &
     return vtx_cell(K, L, L.by_col ? a : b) == cell;
 }
 
+// The 2-D peak rule on the (x, y) grid (8 neighbours, no wrap) for cell with count h.
+__device__ __forceinline__ bool vtx_is_peak(const int32_t *vh, int nb, int cell, int h)
+{
+    const int a = cell / nb, b = cell - (cell / nb) * nb;
+    for (int da = -1; da <= 1; ++da)
+        for (int db = -1; db <= 1; ++db) {
+            if (da == 0 && db == 0)
+                continue;
+            const int aa = a + da, bb = b + db;
+            if (aa < 0 || aa >= nb || bb < 0 || bb >= nb)
+                continue;
+            const int nbc = aa * nb + bb, hn = vh[nbc];
+            if (hn > h || (hn == h && nbc < cell))
+                return false;
+        }
+    return true;
+}
+
 __global__ void __launch_bounds__(kVtxThreads) k_h2_vertex(H2Const K, const trk2d_candidate *cand,
                                                            const VtxLine *geom,
                                                            const int64_t *cand_off,
@@ -332,22 +349,7 @@ __global__ void __launch_bounds__(kVtxThreads) k_h2_vertex(H2Const K, const trk2
         const int h = vh[cell];
         if (h < K.v_threshold)
             continue;
-        const int a = cell / nb, b = cell - (cell / nb) * nb;
-        bool ok = true;
-        for (int da = -1; da <= 1 && ok; ++da)
-            for (int db = -1; db <= 1; ++db) {
-                if (da == 0 && db == 0)
-                    continue;
-                const int aa = a + da, bb = b + db;
-                if (aa < 0 || aa >= nb || bb < 0 || bb >= nb)
-                    continue;
-                const int nbc = aa * nb + bb, hn = vh[nbc];
-                if (hn > h || (hn == h && nbc < cell)) {
-                    ok = false;
-                    break;
-                }
-            }
-        mine += ok;
+        mine += vtx_is_peak(vh, nb, cell, h);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int incl = mine;
@@ -372,23 +374,9 @@ __global__ void __launch_bounds__(kVtxThreads) k_h2_vertex(H2Const K, const trk2
         const int h = vh[cell];
         if (h < K.v_threshold)
             continue;
-        const int a = cell / nb, b = cell - (cell / nb) * nb;
-        bool ok = true;
-        for (int da = -1; da <= 1 && ok; ++da)
-            for (int db = -1; db <= 1; ++db) {
-                if (da == 0 && db == 0)
-                    continue;
-                const int aa = a + da, bb = b + db;
-                if (aa < 0 || aa >= nb || bb < 0 || bb >= nb)
-                    continue;
-                const int nbc = aa * nb + bb, hn = vh[nbc];
-                if (hn > h || (hn == h && nbc < cell)) {
-                    ok = false;
-                    break;
-                }
-            }
-        if (!ok)
+        if (!vtx_is_peak(vh, nb, cell, h))
             continue;
+        const int a = cell / nb, b = cell - (cell / nb) * nb;
         if (idx < K.max_vertices) {
             trk2d_vertex v;
             v.cell = (uint32_t)cell;
@@ -527,14 +515,9 @@ struct trk2d_ctx {
 };
 
 namespace {
-std::mutex g_err_mu;
-std::string g_err;
+thread_local std::string g_err;      // the calling thread's last trk2d_create failure
 
-void set_create_error(const std::string &m)
-{
-    std::lock_guard<std::mutex> lk(g_err_mu);
-    g_err = m;
-}
+void set_create_error(const std::string &m) { g_err = m; }
 
 int fail2(trk2d_ctx *h, int code, const std::string &m)
 {
@@ -885,10 +868,7 @@ extern "C" int trk2d_last_ms(trk2d_ctx *h, float *vote_peak_ms, float *total_ms)
 
 extern "C" const char *trk2d_last_error(const trk2d_ctx *h)
 {
-    if (h)
-        return h->err.c_str();
-    std::lock_guard<std::mutex> lk(g_err_mu);
-    return g_err.c_str();
+    return h ? h->err.c_str() : g_err.c_str();
 }
 
 extern "C" int trk2d_destroy(trk2d_ctx *h)

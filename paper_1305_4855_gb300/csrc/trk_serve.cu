@@ -172,9 +172,11 @@ extern "C" int trk_server_create(trk_server **out, const trk_geometry *geometry,
     S->max_events = lane_options->max_events;
     S->max_hits = lane_options->max_hits;
     S->device = lane_options->device;
+    trk_options lane = *lane_options;
+    lane.fit_candidates = 0;            // served events return candidates and hits only
     for (int l = 0; l < n_lanes; ++l) {
         trk_ctx *h = nullptr;
-        const int rc = trk_create(&h, geometry, binning, lane_options);
+        const int rc = trk_create(&h, geometry, binning, &lane);
         if (rc != TRK_OK) {
             server_free(S);
             return rc;
