@@ -47,7 +47,8 @@ cudaError_t launch_assign(const AssignArgs &A, int n_sm, cudaStream_t s);
 cudaError_t launch_cand_fit(const trk_candidate *cand, const unsigned long long *n_cand,
                             int64_t cand_cap, const int32_t *hit_ids, int64_t hit_cap,
                             const CallArgs *args, double kB, int n_layers, trk_track *out,
-                            uint8_t *hit_used, int n_sm, cudaStream_t s);
+                            uint8_t *hit_used, int32_t *order, int32_t *buckets, int n_sm,
+                            cudaStream_t s);
 cudaError_t prepare_fit_kernel();
 cudaError_t launch_cand_hits(const trk_candidate *cand, const unsigned long long *n_cand,
                              int64_t cand_cap, const int64_t *vote_off, int32_t *assign,
@@ -120,6 +121,8 @@ struct trk_ctx {
     int32_t *d_hit_ids = nullptr;
     trk_track *d_tracks = nullptr;       // candidate fits (fit_candidates)
     uint8_t *d_hit_used = nullptr;       // per hit id: kept by the fit
+    int32_t *d_fit_order = nullptr;      // candidates grouped by hit count
+    int32_t *d_fit_buckets = nullptr;
     int64_t *d_cand_off = nullptr;
     trk_hit *d_in_hits = nullptr;
     int64_t *d_in_offsets = nullptr;
@@ -295,7 +298,7 @@ static void free_all(trk_ctx *h)
                    h->d_cbits,     h->d_filter,     h->d_wprefix,
                    h->d_bsum,      h->d_cand,       h->d_fill,        h->d_vote_off, h->d_assign,
                    h->d_nhits,     h->d_hit_off,    h->d_hit_ids,     h->d_cand_off, h->d_in_hits,
-                   h->d_tracks,    h->d_hit_used,
+                   h->d_tracks,    h->d_hit_used,   h->d_fit_order,   h->d_fit_buckets,
                    h->d_in_offsets, h->d_chunk_pos};
     for (void *p : dev)
         if (p)
@@ -463,6 +466,8 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
     if (o.fit_candidates) {
         ALLOC(d_tracks, o.cand_capacity);
         ALLOC(d_hit_used, o.assign_capacity);
+        ALLOC(d_fit_order, o.cand_capacity);
+        ALLOC(d_fit_buckets, 1024);
     }
     ALLOC(d_cand_off, E + 1);
 #undef ALLOC
@@ -596,7 +601,8 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     if (o.fit_candidates)
         TRK_CUDA(h, launch_cand_fit(h->d_cand, &ctr->n_cand, o.cand_capacity, h->d_hit_ids,
                                     o.assign_capacity, h->d_args, h->C.kB_d, h->geo.n_layers,
-                                    h->d_tracks, h->d_hit_used, h->n_sm, s));
+                                    h->d_tracks, h->d_hit_used, h->d_fit_order,
+                                    h->d_fit_buckets, h->n_sm, s));
     TRK_CUDA(h, launch_finalize(h->d_wprefix, h->W, h->d_args, ctr, o.cand_capacity,
                                 h->d_cand_off, h->d_status, s));
     TRK_CUDA(h, cudaMemcpyAsync(h->h_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));

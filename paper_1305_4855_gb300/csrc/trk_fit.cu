@@ -26,7 +26,70 @@ struct FitTrackArgs {
     double kB;                   // K * B [GeV / cm]
     trk_track *out;
     uint8_t *hit_used;
+    const int32_t *order;        // candidates in processing order (by hit count)
 };
+
+// Candidates are fitted in an order grouped by hit count (a counting sort on
+// min(n_hits, kFitBuckets - 1), largest first), so that the threads of a warp walk hit lists
+// of similar length; the results go to each candidate's own slot, so the order does not
+// change them.
+constexpr int kFitBuckets = 1024;
+
+__device__ __forceinline__ int fit_bucket(int n_hits)
+{
+    const int m = n_hits < 0 ? 0 : (n_hits >= kFitBuckets ? kFitBuckets - 1 : n_hits);
+    return kFitBuckets - 1 - m;
+}
+
+__global__ void k_fit_count(const trk_candidate *cand, const unsigned long long *n_cand,
+                            int64_t cand_cap, int32_t *counts)
+{
+    int64_t n = (int64_t)*n_cand;
+    n = n < cand_cap ? n : cand_cap;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&counts[fit_bucket(cand[c].n_hits)], 1);
+}
+
+// Exclusive scan of the bucket counts in place (one block of kFitBuckets threads).
+__global__ void __launch_bounds__(kFitBuckets) k_fit_scan(int32_t *counts)
+{
+    __shared__ int32_t warp_tot[kFitBuckets / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int v = counts[t];
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o)
+            incl += u;
+    }
+    if (lane == 31)
+        warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int x = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(kFull, x, o);
+            if (lane >= o)
+                x += u;
+        }
+        warp_tot[lane] = x;
+    }
+    __syncthreads();
+    counts[t] = (w > 0 ? warp_tot[w - 1] : 0) + incl - v;
+}
+
+__global__ void k_fit_scatter(const trk_candidate *cand, const unsigned long long *n_cand,
+                              int64_t cand_cap, int32_t *next, int32_t *order)
+{
+    int64_t n = (int64_t)*n_cand;
+    n = n < cand_cap ? n : cand_cap;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x)
+        order[atomicAdd(&next[fit_bucket(cand[c].n_hits)], 1)] = (int32_t)c;
+}
 
 constexpr int kFitThreads = 128;
 
@@ -121,8 +184,9 @@ __global__ void __launch_bounds__(kFitThreads) k_cand_fit(FitTrackArgs A, int n_
     n = n < A.cand_cap ? n : A.cand_cap;
     const trk_hit *H = A.args->hits;
     const int64_t n_hits = A.args->n_hits;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t ci = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ci < n;
+         ci += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = A.order[ci];
         const trk_candidate cd = A.cand[c];
         const int m = cd.n_hits;
         const int64_t off = cd.hit_off;
@@ -279,8 +343,15 @@ __global__ void __launch_bounds__(kFitThreads) k_cand_fit(FitTrackArgs A, int n_
 cudaError_t launch_cand_fit(const trk_candidate *cand, const unsigned long long *n_cand,
                             int64_t cand_cap, const int32_t *hit_ids, int64_t hit_cap,
                             const CallArgs *args, double kB, int n_layers, trk_track *out,
-                            uint8_t *hit_used, int n_sm, cudaStream_t s)
+                            uint8_t *hit_used, int32_t *order, int32_t *buckets, int n_sm,
+                            cudaStream_t s)
 {
+    cudaError_t e = cudaMemsetAsync(buckets, 0, sizeof(int32_t) * kFitBuckets, s);
+    if (e != cudaSuccess)
+        return e;
+    k_fit_count<<<n_sm * 4, 256, 0, s>>>(cand, n_cand, cand_cap, buckets);
+    k_fit_scan<<<1, kFitBuckets, 0, s>>>(buckets);
+    k_fit_scatter<<<n_sm * 4, 256, 0, s>>>(cand, n_cand, cand_cap, buckets, order);
     FitTrackArgs A;
     A.cand = cand;
     A.n_cand = n_cand;
@@ -291,6 +362,7 @@ cudaError_t launch_cand_fit(const trk_candidate *cand, const unsigned long long 
     A.kB = kB;
     A.out = out;
     A.hit_used = hit_used;
+    A.order = order;
     const size_t smem = sizeof(LayerPick) * kFitThreads * (size_t)n_layers;
     k_cand_fit<<<n_sm * 8, kFitThreads, smem, s>>>(A, n_layers);
     return cudaGetLastError();
