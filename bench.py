@@ -29,17 +29,23 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "barrel10_500trk"
 BATCH_WORKLOAD = "barrel10_batch256"
-# Algorithmic FP32 work of the vote kernel, counted from its formulas (add, multiply,
-# fused multiply-add, compare each 1; square root, division, arcsine, arctangent each 1):
+# Algorithmic FP32 work of the vote kernel, counted from its formulas as written: each add,
+# subtract, multiply, fused multiply-add, min, max, abs, compare, square root, reciprocal
+# square root, reciprocal, division, floor, arcsine and arctangent counts 1; selects, sign
+# flips and integer work do not count.
 #   every enumerated triplet: the curvature test (4 differences, D, |v|^2, |w|^2, 3 products,
-#     1 comparison) = 14;
-#   every survivor of it: the transverse fit (circle, q/pT, d0, perigee) = 62 and the
-#     conservative longitudinal bound (truncated arcsine series, interval least squares) = 181;
-#   every survivor of the bound: the transverse fit again (62), the exact longitudinal fit
-#     (signed arc lengths, least-squares line) = 124, phi0 and the five bin indices = 41.
+#     1 comparison; the pair's own terms are computed once per pair) = 14;
+#   every survivor of it: the transverse pre-fit (differences, compensated determinants,
+#     circle, q/pT and d0 with their widened range tests, perigee) = 80, and the
+#     conservative longitudinal bound (three arcs by the truncated series with their error
+#     terms and direction tests = 3 x 33, interval least squares for cot and z0 = 89, set-up
+#     = 9) = 197;
+#   every survivor of the bound: the exact transverse fit = 65, the exact longitudinal fit
+#     (first arc 17, two hit-to-hit arcs with the turn choice 2 x 46, least-squares line and
+#     range tests 37) = 146, phi0 and the five bin indices = 31.
 OPS_PER_TRIPLET = 14
-OPS_PER_FIT = 62 + 181
-OPS_PER_EXACT = 62 + 124 + 41
+OPS_PER_FIT = 80 + 197
+OPS_PER_EXACT = 65 + 146 + 31
 
 
 def parse():
