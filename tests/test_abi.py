@@ -107,3 +107,27 @@ def test_create_rejects_bad_setups(lib_path):
     o2.tile_i = 3
     assert lib.trk_create(C.byref(h), C.byref(geo), C.byref(binning), C.byref(o2)) == trk.TRK_ERR_INVALID
     assert lib.trk_create(None, C.byref(geo), C.byref(binning), C.byref(opt)) == trk.TRK_ERR_INVALID
+
+
+def test_hough2d_create_rejects_bad_configs(lib_path):
+    # the 2-D transforms validate their configuration before any device call
+    from paper_1305_4855_gb300 import events, trk
+    lib = trk.load_library()
+    cfg = events.load_workload("sht_jets")
+    h = C.c_void_p()
+
+    def bad(**kw):
+        c = trk.hough2d_config(cfg, 4, 1000)
+        for k, v in kw.items():
+            setattr(c, k, v)
+        return lib.trk2d_create(C.byref(h), C.byref(c), 0)
+
+    assert bad(lo=-10.0) == trk.TRK_ERR_INVALID                  # straight needs lo = -hi
+    assert b"symmetric" in lib.trk2d_last_error(None)
+    assert bad(n_cols=2) == trk.TRK_ERR_INVALID
+    assert bad(kind=7) == trk.TRK_ERR_INVALID
+    assert bad(threshold=0) == trk.TRK_ERR_INVALID
+    assert bad(vertex_bins=200) == trk.TRK_ERR_INVALID
+    assert bad(kind=trk.TRK2D_CURVED_IP, b_tesla=0.0, lo=-1.0, hi=1.0,
+               vertex_bins=0) == trk.TRK_ERR_INVALID                 # curved needs a field
+    assert lib.trk2d_create(None, None, 0) == trk.TRK_ERR_INVALID
