@@ -160,12 +160,13 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(cfg, batch, seconds):
-    """The FP64 oracle as it stands, on all host cores, over a bounded sample of the
-    workload: the first inner hits of every layer triple, until ~`seconds` of CPU work."""
+def cpu_baseline(cfg, batch, seconds, threads=None):
+    """The FP64 oracle as it stands, on all host cores (or `threads`), over a bounded sample
+    of the workload: the first inner hits of every layer triple, until ~`seconds` of CPU
+    work."""
     import oracle
     setup = oracle.OracleSetup.from_workload(cfg)
-    threads = oracle.max_threads()
+    threads = threads or oracle.max_threads()
     # grow the number of inner hits per layer triple until the run takes long enough
     n_inner = 8
     while True:
@@ -358,6 +359,9 @@ def main():
         trip_s, cores, sample = cpu_baseline(cfg, batch, args.cpu_seconds)
         line["cpu_baseline"] = {"value": trip_s / n_trip, "unit": "events/s", "cores": cores,
                                 "kind": "oracle", "sample": sample}
+        trip_1, _, sample_1 = cpu_baseline(cfg, batch, args.cpu_seconds / 3, threads=1)
+        line["cpu_baseline"]["single_thread"] = {"value": trip_1 / n_trip, "unit": "events/s",
+                                                 "cores": 1, "sample": sample_1}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -215,6 +215,25 @@ __device__ __forceinline__ void line_max3(int32_t *p, int n, int stride)
 
 constexpr int kPeakThreads = 256;
 
+// Division by a fixed divisor d >= 1 through a multiply-high.  With m = ceil(2^32 / d) and
+// e = m d - 2^32 < d, x m / 2^32 = x / d + x e / (d 2^32); when x d < 2^32 the added term
+// is below 1 / d, less than the gap from x / d to the next integer, so the floor is exact.
+struct DivBy {
+    uint32_t m;
+    bool one;
+};
+__device__ __forceinline__ DivBy make_div(uint32_t d)
+{
+    DivBy r;
+    r.one = d <= 1u;
+    r.m = r.one ? 0u : 0xFFFFFFFFu / d + 1u;
+    return r;
+}
+__device__ __forceinline__ uint32_t div_by(uint32_t x, DivBy D)
+{
+    return D.one ? x : __umulhi(x, D.m);
+}
+
 __global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist, int32_t *m3,
                                                              FitConst C, int g0, int td,
                                                              const int32_t *status)
@@ -243,7 +262,8 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist
     // third-slowest axis): element x of the run is global offset (d_start - 1) * plane + x,
     // and zero outside [0, n2 * plane).  Eight loads per thread are issued before the
     // shared-memory stores so that the pass streams instead of waiting on each load.
-    const int total = (rows + 2) * plane;
+    const int total = (rows + 2) * plane;        // < 2^16 (shared-memory sized)
+    const DivBy by4 = make_div((uint32_t)n4);
     const int64_t g_first = (int64_t)(d_start - 1) * plane;
     const int64_t g_end = (int64_t)n2 * plane;
     constexpr int kL = 8;
@@ -258,8 +278,8 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist
 #pragma unroll
         for (int u = 0; u < kL; ++u) {
             const int x = x0 + u * kPeakThreads;
-            if (x < total)
-                sk[x + x / n4] = v[u];       // row-padded: line x / n4, column x % n4
+            if (x < total)                   // row-padded: line x / n4, column x % n4
+                sk[x + (int)div_by((uint32_t)x, by4)] = v[u];
         }
     }
     __syncthreads();
@@ -267,14 +287,14 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist
         line_max3(sk + line * P4, n4, 1);
     __syncthreads();
     for (int line = tid; line < (rows + 2) * n4; line += kPeakThreads) {
-        const int lr = line / n4, i4 = line - lr * n4;
+        const int lr = (int)div_by((uint32_t)line, by4), i4 = line - lr * n4;
         line_max3(sk + lr * n3 * P4 + i4, n3, P4);
     }
     __syncthreads();
     int32_t *out = m3 + (size_t)ge * C.nbins + base + (uint32_t)d_start * C.stride[2];
     const int rs = n3 * P4;
     for (int line = tid; line < plane; line += kPeakThreads) {
-        const int i3 = line / n4, i4 = line - i3 * n4;
+        const int i3 = (int)div_by((uint32_t)line, by4), i4 = line - i3 * n4;
         const int32_t *q = sk + i3 * P4 + i4;
         int prev = q[0], cur = q[rs];
         for (int r = 0; r < rows; ++r) {
