@@ -8,7 +8,10 @@ the CUDA path produced as an input.
                       layer triple, FP64 helix fit, binning, edge-ambiguity flags;
   reconstruct      -- votes, peak rule and hit assignment (reconstruct.py, numpy);
   fit_tracks       -- the candidate fit (trk_oracle.c): algebraic circle fit, one hit per
-                      layer, signed arcs and the least-squares line.
+                      layer, signed arcs and the least-squares line;
+  hough2d          -- the per-hit 2-D transforms (straight lines, curved tracks through the
+                      interaction point) and the vertex transform over straight-line peaks
+                      (numpy, FP64).
 """
 from .core import OracleSetup, enumerate_batch, fit_list, fit_tracks, max_threads  # noqa: F401
 from .reconstruct import (histogram, neighbour_offsets, peaks, assign_hits,  # noqa: F401

@@ -42,6 +42,9 @@
  *     dimension is wrapped into [lo, hi) first.
  * Degenerate triplets (circle centred on the origin, or three equal arc lengths) have
  * no perigee or no slope and are rejected and counted.
+ *
+ * The candidate fit (orc_fit_track, orc_fit_tracks) is defined further down, with its own
+ * readings.
  */
 #include <math.h>
 #include <stdint.h>
