@@ -575,11 +575,11 @@ LAUNCHES_PER_CALL = 1 + 1 + 1 + 3 + 9 + 1 + 1 + 1 + 1 + 1
 # only while the vote-kernel sources hash to the recorded digest, and the traffic is
 # reported as null for a tuning without a record.
 VOTE_TRAFFIC = {"workload": "barrel10_500trk",
-                "sources_sha256": "ba6187615e16eb1afc38f881882ffab33f38076e8bea706a72249eb1505e6696",
+                "sources_sha256": "df33da3eb56316d37a8105065e4a792d7ee4a80d93414d1ebf74b2341dad7125",
                 "records": [{"tile_i": 16, "tile_j": 8, "vote_level": 4,
-                             "bytes": 1.103715e9 + 3.234645e9},
+                             "bytes": 1.147688448e9 + 3.341313024e9},
                             {"tile_i": 8, "tile_j": 16, "vote_level": 4,
-                             "bytes": 1.106165504e9 + 3.238753536e9}]}
+                             "bytes": 1.153451776e9 + 3.343365888e9}]}
 VOTE_SOURCES = ["trk_common.cuh", "trk_vote_kernel.cuh", "trk_vote.cu", "trk_vote_l2.cu",
                 "trk_vote_l3.cu", "trk_vote_l4.cu"]
 

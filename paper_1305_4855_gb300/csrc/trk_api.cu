@@ -101,7 +101,8 @@ struct trk_ctx {
     int32_t *d_status = nullptr;
     int64_t *d_item_off = nullptr;
     int32_t *d_hist = nullptr;
-    uint64_t *d_votes = nullptr;
+    uint32_t *d_vote_bin = nullptr;    // vote list: bins and codes of the same slots
+    uint32_t *d_vote_code = nullptr;
     int32_t *d_chunk_item = nullptr;
     int32_t *d_chunk_count = nullptr;
     int32_t *d_chunk_event = nullptr;
@@ -292,7 +293,7 @@ static int validate(const trk_geometry *g, const trk_binning *b, const trk_optio
 static void free_all(trk_ctx *h)
 {
     void *dev[] = {h->d_geo,       h->d_args,       h->d_ctr,         h->d_packed,   h->d_lay_off,
-                   h->d_ev_begin,  h->d_status,     h->d_item_off,    h->d_hist,     h->d_votes,
+                   h->d_ev_begin,  h->d_status,     h->d_item_off,    h->d_hist,     h->d_vote_bin, h->d_vote_code,
                    h->d_chunk_item, h->d_chunk_count, h->d_chunk_event, h->d_chunk_loc,
                    h->d_m3,        h->d_ties,
                    h->d_cbits,     h->d_filter,     h->d_wprefix,
@@ -445,7 +446,8 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
     ALLOC(d_status, E);
     ALLOC(d_item_off, E * geometry->n_triples + 1);
     ALLOC(d_hist, E * h->nbins);
-    ALLOC(d_votes, h->chunk_cap * 32);
+    ALLOC(d_vote_bin, h->chunk_cap * 32);
+    ALLOC(d_vote_code, h->chunk_cap * 32);
     ALLOC(d_chunk_item, h->chunk_cap);
     ALLOC(d_chunk_count, h->chunk_cap);
     ALLOC(d_chunk_event, h->chunk_cap);
@@ -536,7 +538,8 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     va.args = h->d_args;
     va.status = h->d_status;
     va.hist = h->d_hist;
-    va.votes = h->d_votes;
+    va.vote_bin = h->d_vote_bin;
+    va.vote_code = h->d_vote_code;
     va.chunk_item = h->d_chunk_item;
     va.chunk_count = h->d_chunk_count;
     va.chunk_event = h->d_chunk_event;
@@ -564,7 +567,8 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
                                     h->d_bsum, &ctr->n_assign, s));
     TRK_CUDA(h, mark(h->ev_st[3]));
     AssignArgs aa;
-    aa.votes = h->d_votes;
+    aa.vote_bin = h->d_vote_bin;
+    aa.vote_code = h->d_vote_code;
     aa.chunk_item = h->d_chunk_item;
     aa.chunk_count = h->d_chunk_count;
     aa.chunk_event = h->d_chunk_event;
@@ -828,7 +832,8 @@ extern "C" int trk_get_votes(trk_ctx *h, int32_t *dst, uint32_t *bins, int64_t c
                                        &h->d_ctr->pad[0], s));
     AssignArgs aa;
     std::memset(&aa, 0, sizeof(aa));
-    aa.votes = h->d_votes;
+    aa.vote_bin = h->d_vote_bin;
+    aa.vote_code = h->d_vote_code;
     aa.chunk_item = h->d_chunk_item;
     aa.chunk_count = h->d_chunk_count;
     aa.chunk_cap = h->chunk_cap;

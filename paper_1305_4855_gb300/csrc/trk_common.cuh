@@ -79,9 +79,10 @@ struct VoteChunk {
     int64_t offset;
 };
 
-// Vote record: low 32 bits the bin; high 32 bits the code (i << 28) | (j << 24) | k, with
-// i and j the inner and middle hit within the work item's tile (tiles are at most 16 x 16)
-// and k the outer hit within its layer (< 2^24).
+// A vote is a bin and a code (i << 28) | (j << 24) | k, with i and j the inner and middle
+// hit within the work item's tile (tiles are at most 16 x 16) and k the outer hit within
+// its layer (< 2^24).  The vote list keeps bins and codes in two arrays of the same slots:
+// the assignment streams the bins and reads the codes of candidate votes only.
 __host__ __device__ inline uint32_t vote_code(uint32_t i, uint32_t j, uint32_t k)
 {
     return (i << 28) | (j << 24) | (k & 0xffffffu);
@@ -99,7 +100,8 @@ struct VoteArgs {
     const CallArgs *args;
     int32_t *status;             // per-event status (vote overflow is or-ed in)
     int32_t *hist;               // [event][nbins]
-    uint64_t *votes;             // [chunk_cap * 32]
+    uint32_t *vote_bin;          // [chunk_cap * 32]
+    uint32_t *vote_code;         // [chunk_cap * 32]
     int32_t *chunk_item;         // [chunk_cap] item of each 32-slot chunk (-1: empty)
     int32_t *chunk_count;        // [chunk_cap]
     int32_t *chunk_event;        // [chunk_cap] event of the chunk's item
@@ -126,7 +128,8 @@ __device__ __forceinline__ uint32_t cand_filter_bit(int event, uint32_t bin)
 }
 
 struct AssignArgs {
-    const uint64_t *votes;
+    const uint32_t *vote_bin;
+    const uint32_t *vote_code;
     const int32_t *chunk_item;
     const int32_t *chunk_count;
     const int32_t *chunk_event;
@@ -163,6 +166,64 @@ __device__ __forceinline__ float det2(float a, float b, float c, float d)
     const float e = fmaf(-b, c, w);
     const float f = fmaf(a, d, -w);
     return f + e;
+}
+
+// Elementwise arithmetic on one value (float) or on two (float2).  The per-hit parts of
+// the fit are written once over V and run on float2 for two hits of the same triplet: the
+// packed FP32 instructions of sm_100 and later (add/sub/mul/fma .rn .f32x2) round each
+// half exactly as the scalar instruction does, and issue once for both.  Square roots,
+// reciprocals, transcendentals, comparisons and selections stay per half.
+struct M2 {
+    bool x, y;
+};
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b)
+{
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
+__device__ __forceinline__ float2 vabs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float2 vmin(float2 a, float2 b)
+{
+    return make_float2(fminf(a.x, b.x), fminf(a.y, b.y));
+}
+__device__ __forceinline__ bool vle(float a, float b) { return a <= b; }
+__device__ __forceinline__ M2 vle(float2 a, float2 b) { return {a.x <= b.x, a.y <= b.y}; }
+__device__ __forceinline__ bool vge(float a, float b) { return a >= b; }
+__device__ __forceinline__ M2 vge(float2 a, float2 b) { return {a.x >= b.x, a.y >= b.y}; }
+__device__ __forceinline__ bool vlt(float a, float b) { return a < b; }
+__device__ __forceinline__ M2 vlt(float2 a, float2 b) { return {a.x < b.x, a.y < b.y}; }
+__device__ __forceinline__ bool vnot(bool m) { return !m; }
+__device__ __forceinline__ M2 vnot(M2 m) { return {!m.x, !m.y}; }
+__device__ __forceinline__ float vsel(bool m, float a, float b) { return m ? a : b; }
+__device__ __forceinline__ float2 vsel(M2 m, float2 a, float2 b)
+{
+    return make_float2(m.x ? a.x : b.x, m.y ? a.y : b.y);
+}
+template <class V> __device__ __forceinline__ V bc(float a);
+template <> __device__ __forceinline__ float bc<float>(float a) { return a; }
+template <> __device__ __forceinline__ float2 bc<float2>(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float vsqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ float2 vsqrt(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
+__device__ __forceinline__ float vasin(float a) { return asinf(a); }
+__device__ __forceinline__ float2 vasin(float2 a) { return make_float2(asinf(a.x), asinf(a.y)); }
+
+template <class V>
+__device__ __forceinline__ V det2v(V a, V b, V c, V d)
+{
+    const V w = vmul(b, c);
+    const V e = vfma(vneg(b), c, w);
+    const V f = vfma(a, d, vneg(w));
+    return vadd(f, e);
 }
 
 // Result of the transverse + longitudinal part of the fit, everything but phi0.
@@ -259,13 +320,20 @@ __device__ __forceinline__ float approx_sqrt(float x)
     return x * rsqrtf(fmaxf(x, 1e-30f));
 }
 __device__ __forceinline__ float approx_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float2 approx_sqrt(float2 x)
+{
+    return vmul(x, make_float2(rsqrtf(fmaxf(x.x, 1e-30f)), rsqrtf(fmaxf(x.y, 1e-30f))));
+}
 
 // arcsin(x) / x through the x^6 term of its series: 1 + x^2/6 + 3x^4/40 + 5x^6/112.  The
 // remaining terms are positive and below 0.075 x^8 for x <= 0.71 (the ratio of the
 // remainder to x^8 increases with x and is 0.0750 at x = 0.7).
-__device__ __forceinline__ float asin_over_x_series(float x2)
+template <class V>
+__device__ __forceinline__ V asin_over_x_series(V x2)
 {
-    return fmaf(x2, fmaf(x2, fmaf(x2, 5.0f / 112.0f, 3.0f / 40.0f), 1.0f / 6.0f), 1.0f);
+    return vfma(x2, vfma(x2, vfma(x2, bc<V>(5.0f / 112.0f), bc<V>(3.0f / 40.0f)),
+                         bc<V>(1.0f / 6.0f)),
+                bc<V>(1.0f));
 }
 
 // Range test widened by 1e-4 of the range width and of |p|: for the pre-tests below,
@@ -323,44 +391,60 @@ __device__ __forceinline__ int fit_transverse_bound(const float4 &p1, const floa
     return kPass;
 }
 
+// Signed path length from the perigee to hit(s) (hx, hy), bounded without
+// transcendentals: |s| from a truncated arcsine series -- chord / 2R = x <= 0.7: chord
+// (series of x); beyond, the complementary form R (pi - 2 y series(y)) with
+// y = |(P - c) + (p - c)| / 2R, (bx, by) = p - c -- and E, a rigorous bound on its error
+// (series truncation, FP32 evaluation, and the sign when the direction from P is not
+// resolved).  (ax, ay) = P - c.
+template <class V>
+__device__ __forceinline__ void arc_bound(V hx, V hy, V bx, V by, V ax, V ay, const Trans &t,
+                                          V &sh, V &E)
+{
+    const V dx = vsub(hx, bc<V>(t.px)), dy = vsub(hy, bc<V>(t.py));
+    const V ch = approx_sqrt(vfma(dx, dx, vmul(dy, dy)));
+    const V x = vmul(ch, bc<V>(t.inv2r));
+    // both forms share 2R a series(a^2) with a = x (near) or y (far), and the same
+    // truncation bound 2R a 0.075 a^8; evaluated without a branch (lanes differ)
+    const V sx = vadd(ax, bx), sy = vadd(ay, by);
+    const V y = vmin(vmul(approx_sqrt(vfma(sx, sx, vmul(sy, sy))), bc<V>(t.inv2r)), bc<V>(1.0f));
+    const auto far = vnot(vle(x, bc<V>(0.7f)));
+    const V a = vsel(far, y, x);
+    const V a2 = vmul(a, a), a4 = vmul(a2, a2);
+    const V twoRa = vmul(bc<V>(2.0f * t.R), a);
+    const V arc = vmul(twoRa, asin_over_x_series(a2));
+    const V mag = vsel(far, vfma(bc<V>(t.R), bc<V>(3.14159265f), vneg(arc)), arc);
+    V e = vmul(twoRa, vmul(vmul(bc<V>(0.075f), a4), a4));
+    e = vadd(e, vfma(bc<V>(4e-6f), mag, bc<V>(1e-6f * t.R)));
+    const V pr = det2v(dx, dy, bc<V>(t.cx), bc<V>(t.cy));
+    // direction from P not resolved: either sign
+    const V lim = vmul(vmul(bc<V>(1e-3f), ch), bc<V>(t.cn));
+    e = vsel(vle(vabs(pr), lim), vadd(e, vmul(bc<V>(2.0f), mag)), e);
+    sh = vsel(vge(vmul(bc<V>(t.sgn), pr), bc<V>(0.0f)), mag, vneg(mag));
+    E = e;
+}
+
 // Conservative longitudinal test without transcendentals: may the triplet's (cot, z0) be
-// in range?  Each |s_k| is replaced by a truncated arcsine series -- chord / 2R = x <= 0.7:
-// chord (series of x); beyond, the complementary form R (pi - 2 y series(y)) with
-// y = |(P - c) + (p_k - c)| / 2R -- with a rigorous bound on the truncation, a margin for
-// the FP32 evaluation, and interval arithmetic over the least-squares line.  false =
-// certainly outside the cot or z0 range (the exact fit would reject it).
+// in range?  Each s_k is bounded by arc_bound (hits 1 and 2 as a pair, hit 3 alone), and
+// interval arithmetic runs over the least-squares line.  false = certainly outside the
+// cot or z0 range (the exact fit would reject it).
 __device__ __forceinline__ bool z_may_accept(const float4 &p1, const float4 &p2, const float4 &p3,
                                              const Trans &t, const FitConst &C)
 {
-    const float4 *pk[3] = {&p1, &p2, &p3};
     const float rcn = approx_rcp(t.cn);
     const float ax = -t.R * t.cx * rcn, ay = -t.R * t.cy * rcn;          // P - c
-    const float bxs[3] = {-t.cpx, t.ux - t.cpx, t.vx - t.cpx};
-    const float bys[3] = {-t.cpy, t.uy - t.cpy, t.vy - t.cpy};
     float sh[3], E[3];
-    const float twoR = 2.0f * t.R;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float dx = pk[k]->x - t.px, dy = pk[k]->y - t.py;
-        const float ch = approx_sqrt(fmaf(dx, dx, dy * dy));
-        const float x = ch * t.inv2r;
-        // both forms share 2R a series(a^2) with a = x (near) or y (far), and the same
-        // truncation bound 2R a 0.075 a^8; evaluated without a branch (lanes differ)
-        const float sx = ax + bxs[k], sy = ay + bys[k];
-        const float y = fminf(approx_sqrt(fmaf(sx, sx, sy * sy)) * t.inv2r, 1.0f);
-        const bool far = !(x <= 0.7f);
-        const float a = far ? y : x;
-        const float a2 = a * a, a4 = a2 * a2;
-        const float arc = twoR * a * asin_over_x_series(a2);
-        const float mag = far ? fmaf(t.R, 3.14159265f, -arc) : arc;
-        float e = twoR * a * (0.075f * a4 * a4);
-        e += fmaf(4e-6f, mag, 1e-6f * t.R);
-        const float pr = det2(dx, dy, t.cx, t.cy);
-        if (fabsf(pr) <= 1e-3f * ch * t.cn)
-            e += 2.0f * mag;                   // direction from P not resolved
-        sh[k] = (t.sgn * pr >= 0.0f) ? mag : -mag;
-        E[k] = e;
+    {
+        float2 s2, e2;
+        arc_bound(make_float2(p1.x, p2.x), make_float2(p1.y, p2.y),
+                  make_float2(-t.cpx, t.ux - t.cpx), make_float2(-t.cpy, t.uy - t.cpy),
+                  make_float2(ax, ax), make_float2(ay, ay), t, s2, e2);
+        sh[0] = s2.x;
+        sh[1] = s2.y;
+        E[0] = e2.x;
+        E[1] = e2.y;
     }
+    arc_bound(p3.x, p3.y, t.vx - t.cpx, t.vy - t.cpy, ax, ay, t, sh[2], E[2]);
     const float zbar = (p1.z + p2.z + p3.z) * (1.0f / 3.0f);
     const float sbar = (sh[0] + sh[1] + sh[2]) * (1.0f / 3.0f);
     const float eb = (E[0] + E[1] + E[2]) * (1.0f / 3.0f);
@@ -399,13 +483,14 @@ __device__ __forceinline__ bool z_may_accept(const float4 &p1, const float4 &p2,
 // Central angle (0 .. pi) of the arc from P to a hit `chord` away, with `sumlen` the
 // length of (P - c) + (p - c): 2 asin(chord / 2R) up to x = 0.7, and pi - 2 asin(sumlen /
 // 2R) beyond, where the first form is ill-conditioned in FP32.
-__device__ __forceinline__ float central_angle(float chord, float sumlen, float inv2r)
+template <class V>
+__device__ __forceinline__ V central_angle(V chord, V sumlen, float inv2r)
 {
-    const float x = chord * inv2r;
-    const bool far = !(x <= 0.7f);
-    const float arg = far ? fminf(sumlen * inv2r, 1.0f) : x;
-    const float h = 2.0f * asinf(arg);
-    return far ? 3.14159265f - h : h;
+    const V x = vmul(chord, bc<V>(inv2r));
+    const auto far = vnot(vle(x, bc<V>(0.7f)));
+    const V arg = vsel(far, vmin(vmul(sumlen, bc<V>(inv2r)), bc<V>(1.0f)), x);
+    const V h = vmul(bc<V>(2.0f), vasin(arg));
+    return vsel(far, vsub(bc<V>(3.14159265f), h), h);
 }
 
 // Accurate longitudinal part: signed path lengths from P and the least-squares line.
@@ -430,35 +515,34 @@ __device__ __forceinline__ int fit_longitudinal(const float4 &p1, const float4 &
     const float th0 = central_angle(ch0, sqrtf(fmaf(sx, sx, sy * sy)), t.inv2r);
     const float s0 = (t.sgn * det2(dx0, dy0, t.cx, t.cy) >= 0.0f) ? t.R * th0 : -t.R * th0;
     const float turn = 6.2831853f * t.R;
-    const float4 *pk[3] = {&p1, &p2, &p3};
-    float dl[3];
-    dl[0] = 0.0f;
-#pragma unroll
-    for (int k = 1; k < 3; ++k) {
-        const float ex = k == 1 ? t.ux : t.vx, ey = k == 1 ? t.uy : t.vy;
-        const float ee = k == 1 ? t.uu : t.vv;
-        const float cr = det2(b0x, b0y, ex, ey);
-        // (p1 - c) + (p_k - c) = 2 b + e for the complementary (long-chord) form
-        const float qx = fmaf(2.0f, b0x, ex), qy = fmaf(2.0f, b0y, ey);
-        const float psi = central_angle(sqrtf(ee), sqrtf(fmaf(qx, qx, qy * qy)), t.inv2r);
-        const float d = (t.sgn * cr >= 0.0f) ? t.R * psi : -t.R * psi;
-        // crude s_k (good to a fraction of pi R): chord (1 + x^2/6) with its sign
-        const float dx = pk[k]->x - t.px, dy = pk[k]->y - t.py;
-        const float ch = sqrtf(fmaf(dx, dx, dy * dy));
-        const float xk = ch * t.inv2r;
-        const float mag = ch * fmaf(xk * xk, 1.0f / 6.0f, 1.0f);
-        const float crude = (t.sgn * det2(dx, dy, t.cx, t.cy) >= 0.0f) ? mag : -mag;
-        const float want = crude - s0;
-        float best = d, berr = fabsf(d - want);
-        const float dm = d - turn, dp = d + turn;
-        if (fabsf(dm - want) < berr) {
-            best = dm;
-            berr = fabsf(dm - want);
-        }
-        if (fabsf(dp - want) < berr)
-            best = dp;
-        dl[k] = best;
-    }
+    // hits 2 and 3 as a pair (.x, .y)
+    const float2 ex = make_float2(t.ux, t.vx), ey = make_float2(t.uy, t.vy);
+    const float2 ee = make_float2(t.uu, t.vv);
+    const float2 cr = det2v(bc<float2>(b0x), bc<float2>(b0y), ex, ey);
+    // (p1 - c) + (p_k - c) = 2 b + e for the complementary (long-chord) form
+    const float2 qx = vfma(bc<float2>(2.0f), bc<float2>(b0x), ex);
+    const float2 qy = vfma(bc<float2>(2.0f), bc<float2>(b0y), ey);
+    const float2 psi = central_angle(vsqrt(ee), vsqrt(vfma(qx, qx, vmul(qy, qy))), t.inv2r);
+    const float2 d = vsel(vge(vmul(bc<float2>(t.sgn), cr), bc<float2>(0.0f)),
+                          vmul(bc<float2>(t.R), psi), vmul(bc<float2>(-t.R), psi));
+    // crude s_k (good to a fraction of pi R): chord (1 + x^2/6) with its sign
+    const float2 dx = vsub(make_float2(p2.x, p3.x), bc<float2>(t.px));
+    const float2 dy = vsub(make_float2(p2.y, p3.y), bc<float2>(t.py));
+    const float2 ch = vsqrt(vfma(dx, dx, vmul(dy, dy)));
+    const float2 xk = vmul(ch, bc<float2>(t.inv2r));
+    const float2 mag = vmul(ch, vfma(vmul(xk, xk), bc<float2>(1.0f / 6.0f), bc<float2>(1.0f)));
+    const float2 crude =
+        vsel(vge(vmul(bc<float2>(t.sgn), det2v(dx, dy, bc<float2>(t.cx), bc<float2>(t.cy))),
+                 bc<float2>(0.0f)),
+             mag, vneg(mag));
+    const float2 want = vsub(crude, bc<float2>(s0));
+    // the first of d, d - turn, d + turn closest to the crude estimate
+    const float2 dm = vsub(d, bc<float2>(turn)), dp = vadd(d, bc<float2>(turn));
+    const float2 e0 = vabs(vsub(d, want)), em = vabs(vsub(dm, want)), ep = vabs(vsub(dp, want));
+    const M2 take_m = vlt(em, e0);
+    const float2 best = vsel(take_m, dm, d), berr = vsel(take_m, em, e0);
+    const float2 dl12 = vsel(vlt(ep, berr), dp, best);
+    const float dl[3] = {0.0f, dl12.x, dl12.y};
     const float dbar = (dl[1] + dl[2]) * (1.0f / 3.0f);
     const float sbar = s0 + dbar;
     const float zbar = (p1.z + p2.z + p3.z) * (1.0f / 3.0f);

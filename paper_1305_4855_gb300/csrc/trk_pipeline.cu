@@ -617,66 +617,68 @@ __global__ void __launch_bounds__(kAssignThreads, 1) k_assign_fill(AssignArgs A)
     const int64_t n_slots = n_chunks * kWarp;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // Only ~1 % of the votes land in candidate bins, so the kernel is a stream over the
-    // vote list.  Each thread takes kP pairs of adjacent vote slots (one 16-byte load each,
-    // a warp covers two whole 32-slot chunks) a grid stride apart and issues their vote,
-    // chunk count and chunk event loads together; votes are read once, with the streaming
-    // (evict-first) hint.  Slots past a chunk's count hold stale data and are discarded.
-    // The shared-memory candidate filter then leaves the bitmap lookup (a random 32-byte
-    // L2 sector per vote) to the few votes whose filter bit is set.
-    constexpr int kP = 4, kU = 2 * kP;
-    const int64_t n_pairs = n_slots / 2;
-    for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p0 < n_pairs;
-         p0 += kP * stride) {
-        uint64_t v[kU];
-        int ev[kU];
-        int cnt[kU];
+    // bins of the vote list.  Each thread takes kP groups of four adjacent slots (one
+    // 16-byte load each; a warp covers four whole 32-slot chunks) a grid stride apart and
+    // issues their bin, chunk count and chunk event loads together; bins are read once,
+    // with the streaming (evict-first) hint.  Slots past a chunk's count hold stale data
+    // and are discarded.  The shared-memory candidate filter then leaves the bitmap lookup
+    // (a random 32-byte L2 sector per vote) to the few votes whose filter bit is set, and
+    // only candidate votes read their code.
+    constexpr int kP = 4, kU = 4 * kP;
+    const int64_t n_quads = n_slots / 4;
+    for (int64_t q0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q0 < n_quads;
+         q0 += kP * stride) {
+        uint32_t bin[kU];
+        int ev[kP];
+        int cnt[kP];
 #pragma unroll
         for (int u = 0; u < kP; ++u) {
-            const int64_t pr = p0 + u * stride;
-            const bool in = pr < n_pairs;
-            const int64_t slot = 2 * pr;
-            ulonglong2 two = make_ulonglong2(0ull, 0ull);
+            const int64_t qd = q0 + u * stride;
+            const bool in = qd < n_quads;
+            uint4 four = make_uint4(0u, 0u, 0u, 0u);
             if (in)
-                two = __ldcs(reinterpret_cast<const ulonglong2 *>(A.votes) + pr);
-            v[2 * u] = two.x;
-            v[2 * u + 1] = two.y;
-            cnt[2 * u] = cnt[2 * u + 1] = in ? __ldg(A.chunk_count + (slot >> 5)) : 0;
-            ev[2 * u] = ev[2 * u + 1] = in ? __ldg(A.chunk_event + (slot >> 5)) : 0;
+                four = __ldcs(reinterpret_cast<const uint4 *>(A.vote_bin) + qd);
+            bin[4 * u] = four.x;
+            bin[4 * u + 1] = four.y;
+            bin[4 * u + 2] = four.z;
+            bin[4 * u + 3] = four.w;
+            cnt[u] = in ? __ldg(A.chunk_count + (qd >> 3)) : 0;
+            ev[u] = in ? __ldg(A.chunk_event + (qd >> 3)) : 0;
         }
+        // slot within its chunk of vote r of group u: 4 (qd & 7) + r
+        const int sub = 4 * (int)(q0 & 7);
+        // bitmap word of each vote whose filter bit is set (0 for the others)
         uint32_t word[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int64_t slot = 2 * (p0 + (u >> 1) * stride) + (u & 1);
-            const uint32_t bin = (uint32_t)v[u];
-            if ((int)(slot & 31) >= cnt[u]) {
-                ev[u] = -1;
-            } else {
-                const uint32_t fb = cand_filter_bit(ev[u], bin);
-                if (!((s_filter[fb >> 5] >> (fb & 31)) & 1u))
-                    ev[u] = -1;
+        for (int r = 0; r < kU; ++r) {
+            const int u = r >> 2;
+            bool look = false;
+            if (sub + (r & 3) < cnt[u]) {
+                const uint32_t fb = cand_filter_bit(ev[u], bin[r]);
+                look = (s_filter[fb >> 5] >> (fb & 31)) & 1u;
             }
-            word[u] = ev[u] >= 0 ? __ldg(A.cbits + (size_t)ev[u] * A.W + (bin >> 5)) : 0u;
+            word[r] = look ? __ldg(A.cbits + (size_t)ev[u] * A.W + (bin[r] >> 5)) : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int64_t slot = 2 * (p0 + (u >> 1) * stride) + (u & 1);
-            const uint32_t bin = (uint32_t)v[u];
-            if (ev[u] < 0 || !((word[u] >> (bin & 31)) & 1u))
+        for (int r = 0; r < kU; ++r) {
+            const int u = r >> 2;
+            if (!((word[r] >> (bin[r] & 31)) & 1u))
                 continue;
             const int e = ev[u];
-            const size_t wpos = (size_t)e * A.W + (bin >> 5);
+            const size_t wpos = (size_t)e * A.W + (bin[r] >> 5);
             const int64_t c =
-                (int64_t)A.wprefix[wpos] + __popc(word[u] & ((1u << (bin & 31)) - 1u));
+                (int64_t)A.wprefix[wpos] + __popc(word[r] & ((1u << (bin[r] & 31)) - 1u));
             if (c >= A.cand_cap)
                 continue;
+            const int64_t slot = 4 * (q0 + u * stride) + (r & 3);
             const int4 loc = __ldg(A.chunk_loc + (slot >> 5));
+            const uint32_t code = __ldg(A.vote_code + slot);
             const int fslot = atomicAdd(&A.fill[c], 1);
             const int64_t pos = A.vote_off[c] + 3 * (int64_t)fslot;
             if (pos + 3 > A.assign_cap) {
                 atomicOr(&A.ctr->overflow, 2ull);
                 continue;
             }
-            const uint32_t code = (uint32_t)(v[u] >> 32);
             const int ip = loc.x + (int)code_i(code);
             const int jp = loc.y + (int)code_j(code);
             const int kp = loc.z + (int)code_k(code);
@@ -803,13 +805,12 @@ __global__ void k_decode_votes(AssignArgs A, const int64_t *chunk_pos, int64_t n
         const int64_t out = chunk_pos[cid] + lane;
         if (out >= cap)
             continue;
-        const uint64_t v = A.votes[cid * kWarp + lane];
-        const uint32_t code = (uint32_t)(v >> 32);
+        const uint32_t code = A.vote_code[cid * kWarp + lane];
         dst[4 * out] = loc.e;
         dst[4 * out + 1] = __float_as_int(A.packed[loc.a_first + (int)code_i(code)].w);
         dst[4 * out + 2] = __float_as_int(A.packed[loc.b_first + (int)code_j(code)].w);
         dst[4 * out + 3] = __float_as_int(A.packed[loc.c_first + (int)code_k(code)].w);
-        bins[out] = (uint32_t)v;
+        bins[out] = A.vote_bin[cid * kWarp + lane];
     }
 }
 

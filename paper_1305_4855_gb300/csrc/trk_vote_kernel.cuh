@@ -57,8 +57,11 @@ __device__ __forceinline__ void flush_votes(const VoteArgs &A, WarpQueues<NW> &Q
     ws.res_chunk++;
     ws.res_left--;
     if (cid < A.chunk_cap) {
-        if (lane < count)
-            A.votes[cid * kWarp + lane] = Q.stg[w][(ws.hs + lane) & (kRing - 1)];
+        if (lane < count) {
+            const uint64_t v = Q.stg[w][(ws.hs + lane) & (kRing - 1)];
+            A.vote_bin[cid * kWarp + lane] = (uint32_t)v;
+            A.vote_code[cid * kWarp + lane] = (uint32_t)(v >> 32);
+        }
         if (lane == 0) {
             A.chunk_item[cid] = item;
             A.chunk_count[cid] = count;
