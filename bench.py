@@ -46,6 +46,17 @@ BATCH_WORKLOAD = "barrel10_batch256"
 OPS_PER_TRIPLET = 14
 OPS_PER_FIT = 80 + 197
 OPS_PER_EXACT = 65 + 146 + 31
+# Of those, the operations that go to the special-function (MUFU) pipe, the co-bound
+# (16 per SM per clock): square roots, reciprocal square roots, reciprocals, divisions,
+# arcsines and arctangents.
+#   every survivor of the curvature test: the pre-fit's 2 square roots and 4 reciprocals,
+#     the bound's reciprocal of |c|, 2 square roots per arc and the 2 square roots and 2
+#     reciprocals of the interval line = 17;
+#   every survivor of the bound: the exact transverse fit's 2 square roots and 4 divisions,
+#     the longitudinal fit's 1 reciprocal, 8 square roots, 3 arcsines and 1 division, and
+#     phi0's arctangent = 20.
+MUFU_PER_FIT = 6 + 11
+MUFU_PER_EXACT = 6 + 13 + 1
 
 
 def parse():
@@ -326,6 +337,9 @@ def main():
     alg_ops = (OPS_PER_TRIPLET * stats["n_triplets"] + OPS_PER_FIT * stats["n_fit"] +
                OPS_PER_EXACT * stats["n_exact"]) / 1e12
     achieved = alg_ops / (vote_ms / 1000.0) if vote_ms else None
+    mufu_peak = sm_count * 16 * sm_mhz * 1e6 / 1e12
+    mufu_ops = (MUFU_PER_FIT * stats["n_fit"] + MUFU_PER_EXACT * stats["n_exact"]) / 1e12
+    mufu = mufu_ops / (vote_ms / 1000.0) if vote_ms else None
     line = {
         "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -345,7 +359,12 @@ def main():
                                    % (sm_count, sm_mhz),
                      "achieved_basis": "%d FP32 ops per enumerated triplet + %d per fit + %d per "
                                        "exact fit (vote kernel stats of the call)"
-                                       % (OPS_PER_TRIPLET, OPS_PER_FIT, OPS_PER_EXACT)},
+                                       % (OPS_PER_TRIPLET, OPS_PER_FIT, OPS_PER_EXACT),
+                     "mufu": {"achieved": mufu, "peak": mufu_peak, "unit": "T ops/s",
+                              "frac": (mufu / mufu_peak) if mufu else None,
+                              "basis": "%d special-function ops per fit + %d per exact fit; "
+                                       "%d SMs x 16 per clock" % (MUFU_PER_FIT, MUFU_PER_EXACT,
+                                                                  sm_count)}},
         "e2e": {"value": world * args.steps / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "stage_ms": stage_ms,
