@@ -5,9 +5,11 @@
 // Persistent blocks pull work items (event, layer triple, tile of inner x middle hits)
 // from a device counter.  Each thread owns one (inner, middle) hit pair and walks the
 // outer-layer hits, staged in shared memory, through three stages:
-//   A  curvature prefilter (13 FP32 ops): a superset test of the q/pT range;
-//   B  the full FP32 fit up to (q/pT, d0, cot, z0) with early range rejections;
-//   C  phi0, the five bin indices, the histogram atomic and the vote-list record.
+//   A  curvature prefilter (14 FP32 ops): a superset test of the q/pT range;
+//   B  the transverse pre-fit and the conservative longitudinal bound (superset tests of
+//      the q/pT, d0, cot and z0 ranges);
+//   C  the exact FP32 fit, phi0, the five bin indices, the histogram atomic and the
+//      vote-list record.
 // Between stages the surviving (pair, hit) items are compacted into per-warp ring
 // queues in shared memory so that B and C run with all 32 lanes busy.  Fits that the
 // FP32 path cannot resolve (near-collinear, degenerate) are recomputed in FP64.
