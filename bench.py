@@ -543,8 +543,8 @@ def run_served(args, cfg, batch, capacity, local):
              "offered_100kHz": float(cfg.get("serving", {}).get("arrival_rate_hz", 100000.0))}
     serving_cfg = dict(cfg)
     for name, rate in rates.items():
-        # lanes launch eagerly: batch sizes vary, and a first-use graph capture per size
-        # would land in the latency tail
+        # lanes launch eagerly (the server ignores use_graph): batch sizes vary, and a
+        # first-use graph capture per size would land in the latency tail
         srv = Server(serving_cfg, lane_events=4, lane_hits=4 * per_event_max, n_lanes=4,
                      use_graph=0,
                      device=local, vote_capacity=1 << 31, cand_capacity=1 << 21,

@@ -100,7 +100,11 @@ typedef struct trk_options {
                                                in {64, 128, 256} */
     int32_t k_chunk;                        /* outer-layer hits staged per shared chunk */
     int32_t blocks_per_sm;                  /* persistent vote blocks per SM (0: auto) */
-    int32_t use_graph;                      /* capture each call shape in a CUDA graph */
+    int32_t use_graph;                      /* capture each call shape in a CUDA graph (the
+                                               capture runs in the calling thread; do not
+                                               create or destroy handles in other threads
+                                               meanwhile: trk_destroy synchronises the
+                                               device) */
     int32_t vote_level;                     /* vote kernel occupancy: 2, 3 or 4 blocks of 256
                                                threads per SM (0: 3) */
     int32_t fit_candidates;                 /* 1: fit a helix to every candidate's hits in
@@ -282,7 +286,11 @@ typedef struct trk_served_event {
 } trk_served_event;
 
 /* Create a server of n_lanes (1..16) lanes; each lane allocates one trk handle with
- * lane_options (fit_candidates is ignored: served events return candidates and hits). */
+ * lane_options.  fit_candidates is ignored (served events return candidates and hits), and
+ * so is use_graph: lanes launch their kernels directly.  A lane runs in its own thread, and
+ * while a stream of the process is capturing a CUDA graph, device-wide synchronisation
+ * anywhere in the process (handle creation or destruction in another thread, for one) is
+ * invalid. */
 int trk_server_create(trk_server **out, const trk_geometry *geometry, const trk_binning *binning,
                       const trk_options *lane_options, int32_t n_lanes);
 

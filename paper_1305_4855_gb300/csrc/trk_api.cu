@@ -482,20 +482,29 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
         return fail(nullptr, TRK_ERR_NOMEM, "cudaMallocHost failed");
     }
     std::memset(h->h_ctr, 0, sizeof(Counters));
-    if (cudaMemcpy(h->d_geo, &dg, sizeof(dg), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
-        cudaStreamCreate(&h->own_stream) != cudaSuccess ||
-        cudaEventCreate(&h->ev_st[0]) != cudaSuccess || cudaEventCreate(&h->ev_st[1]) != cudaSuccess ||
-        cudaEventCreate(&h->ev_st[2]) != cudaSuccess || cudaEventCreate(&h->ev_st[3]) != cudaSuccess ||
-        cudaEventCreate(&h->ev_st[4]) != cudaSuccess ||
-        prepare_pipeline_kernels() != cudaSuccess || prepare_fit_kernel() != cudaSuccess ||
-        cudaMemset(h->d_hist, 0, sizeof(int32_t) * (size_t)(E * h->nbins)) != cudaSuccess ||
-        cudaMemset(h->d_chunk_item, 0xff, sizeof(int32_t) * (size_t)h->chunk_cap) != cudaSuccess ||
-        cudaMemset(h->d_chunk_count, 0, sizeof(int32_t) * (size_t)h->chunk_cap) != cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess) {
-        free_all(h);
-        delete h;
-        return fail(nullptr, TRK_ERR_CUDA, "initialisation failed");
+    // initialisation on the handle's own non-blocking stream, synchronised on that stream
+    // only: a device-wide synchronisation would be invalid while another thread captures
+    cudaError_t ie = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+    cudaStream_t is = h->own_stream;
+    const cudaError_t init[] = {
+        ie,
+        cudaMemcpyAsync(h->d_geo, &dg, sizeof(dg), cudaMemcpyHostToDevice, is),
+        cudaEventCreate(&h->ev0), cudaEventCreate(&h->ev1),
+        cudaEventCreate(&h->ev_st[0]), cudaEventCreate(&h->ev_st[1]),
+        cudaEventCreate(&h->ev_st[2]), cudaEventCreate(&h->ev_st[3]),
+        cudaEventCreate(&h->ev_st[4]),
+        prepare_pipeline_kernels(), prepare_fit_kernel(),
+        cudaMemsetAsync(h->d_hist, 0, sizeof(int32_t) * (size_t)(E * h->nbins), is),
+        cudaMemsetAsync(h->d_chunk_item, 0xff, sizeof(int32_t) * (size_t)h->chunk_cap, is),
+        cudaMemsetAsync(h->d_chunk_count, 0, sizeof(int32_t) * (size_t)h->chunk_cap, is),
+        cudaStreamSynchronize(is)};
+    for (cudaError_t r : init) {
+        if (r != cudaSuccess) {
+            free_all(h);
+            delete h;
+            return fail(nullptr, TRK_ERR_CUDA,
+                        std::string("initialisation failed: ") + cudaGetErrorString(r));
+        }
     }
     *out = h;
     return TRK_OK;

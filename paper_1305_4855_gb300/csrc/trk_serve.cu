@@ -174,6 +174,8 @@ extern "C" int trk_server_create(trk_server **out, const trk_geometry *geometry,
     S->device = lane_options->device;
     trk_options lane = *lane_options;
     lane.fit_candidates = 0;            // served events return candidates and hits only
+    lane.use_graph = 0;                 // no capture in lane threads: it would make device-
+                                        // wide synchronisation elsewhere in the process invalid
     for (int l = 0; l < n_lanes; ++l) {
         trk_ctx *h = nullptr;
         const int rc = trk_create(&h, geometry, binning, &lane);
