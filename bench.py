@@ -594,7 +594,7 @@ LAUNCHES_PER_CALL = 1 + 1 + 1 + 3 + 9 + 1 + 1 + 1 + 1 + 1
 # only while the vote-kernel sources hash to the recorded digest, and the traffic is
 # reported as null for a tuning without a record.
 VOTE_TRAFFIC = {"workload": "barrel10_500trk",
-                "sources_sha256": "ced46136d4e92302d626ae9a12a250798228cb53224bfee50e3097f2f90bd366",
+                "sources_sha256": "051b1fac3c55527392170c891262a8c348833f0bef334e42e9ebdd77e4b98992",
                 "records": [{"tile_i": 16, "tile_j": 8, "vote_level": 4,
                              "bytes": 1.147688448e9 + 3.341313024e9},
                             {"tile_i": 8, "tile_j": 16, "vote_level": 4,

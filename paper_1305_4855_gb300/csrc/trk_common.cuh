@@ -169,10 +169,11 @@ __device__ __forceinline__ float det2(float a, float b, float c, float d)
 }
 
 // Elementwise arithmetic on one value (float) or on two (float2).  The per-hit parts of
-// the fit are written once over V and run on float2 for two hits of the same triplet: the
-// packed FP32 instructions of sm_100 and later (add/sub/mul/fma .rn .f32x2) round each
-// half exactly as the scalar instruction does, and issue once for both.  Square roots,
-// reciprocals, transcendentals, comparisons and selections stay per half.
+// the fit are written once over V and run on float2 for two hits of the same triplet.  The
+// packed FP32 instructions of sm_100 and later (add/mul/fma .rn .f32x2; a subtraction is
+// the addition of the negated operand, which is exact) round each half exactly as the
+// scalar instruction does, and issue once for both.  Square roots, reciprocals,
+// transcendentals, comparisons and selections stay per half.
 struct M2 {
     bool x, y;
 };
@@ -217,6 +218,7 @@ __device__ __forceinline__ float2 vsqrt(float2 a) { return make_float2(sqrtf(a.x
 __device__ __forceinline__ float vasin(float a) { return asinf(a); }
 __device__ __forceinline__ float2 vasin(float2 a) { return make_float2(asinf(a.x), asinf(a.y)); }
 
+// det2 (below) over V: a*d - b*c by Kahan's FMA determinant, per half for float2.
 template <class V>
 __device__ __forceinline__ V det2v(V a, V b, V c, V d)
 {
