@@ -594,11 +594,9 @@ LAUNCHES_PER_CALL = 1 + 1 + 1 + 3 + 9 + 1 + 1 + 1 + 1 + 1
 # only while the vote-kernel sources hash to the recorded digest, and the traffic is
 # reported as null for a tuning without a record.
 VOTE_TRAFFIC = {"workload": "barrel10_500trk",
-                "sources_sha256": "051b1fac3c55527392170c891262a8c348833f0bef334e42e9ebdd77e4b98992",
-                "records": [{"tile_i": 16, "tile_j": 8, "vote_level": 4,
-                             "bytes": 1.147688448e9 + 3.341313024e9},
-                            {"tile_i": 8, "tile_j": 16, "vote_level": 4,
-                             "bytes": 1.153451776e9 + 3.343365888e9}]}
+                "sources_sha256": "eee6430b476e2a3ad60cd5f5af4b5c6c00c1684c19f0f69b67a510746f6da6cd",
+                "records": [{"tile_i": 8, "tile_j": 16, "vote_level": 4,
+                             "bytes": 1.11732864e9 + 3.241699072e9}]}
 VOTE_SOURCES = ["trk_common.cuh", "trk_vote_kernel.cuh", "trk_vote.cu", "trk_vote_l2.cu",
                 "trk_vote_l3.cu", "trk_vote_l4.cu"]
 

@@ -213,8 +213,6 @@ __device__ __forceinline__ float2 vsel(M2 m, float2 a, float2 b)
 template <class V> __device__ __forceinline__ V bc(float a);
 template <> __device__ __forceinline__ float bc<float>(float a) { return a; }
 template <> __device__ __forceinline__ float2 bc<float2>(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float vsqrt(float a) { return sqrtf(a); }
-__device__ __forceinline__ float2 vsqrt(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
 __device__ __forceinline__ float vasin(float a) { return asinf(a); }
 __device__ __forceinline__ float2 vasin(float2 a) { return make_float2(asinf(a.x), asinf(a.y)); }
 
@@ -259,6 +257,22 @@ __device__ __forceinline__ bool in_range_f32(const FitConst &C, int k, float p)
     return p >= C.lo[k] && p < C.hi[k];
 }
 
+// Square root and reciprocal through the MUFU approximations: rsqrtf and the reciprocal
+// of __fdividef are within 2 ulp, so each result is within about 3e-7 relative, 30 times
+// inside the 1e-5 parameter tolerance.  Both the fit and the conservative bounds use them
+// (the bounds' margins are 1e-4); correctly rounded square roots and divisions would cost
+// several times the instructions in a kernel bound by instruction issue.
+__device__ __forceinline__ float approx_sqrt(float x)
+{
+    return x * rsqrtf(fmaxf(x, 1e-30f));
+}
+__device__ __forceinline__ float approx_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float approx_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float2 approx_sqrt(float2 x)
+{
+    return vmul(x, make_float2(rsqrtf(fmaxf(x.x, 1e-30f)), rsqrtf(fmaxf(x.y, 1e-30f))));
+}
+
 // Transverse part of the fit: circle, q/pT, d0 and the perigee.
 struct Trans {
     float ux, uy, vx, vy, uu, vv;
@@ -285,23 +299,23 @@ __device__ __forceinline__ int fit_transverse(const float4 &p1, const float4 &p2
     if (D * D <= C.sag2 * t.vv)
         return kNeedFp64;
     // q/pT = -sign(D) / (K B R), R = |u||v||w| / (2|D|)
-    const float sq = sqrtf(t.uu * t.vv * ww);
-    const float rq = 1.0f / sq;
+    const float sq = approx_sqrt(t.uu * t.vv * ww);
+    const float rq = approx_rcp(sq);
     t.qopt = (-2.0f * D) * rq * C.inv_kB;
     if (!in_range_f32(C, 1, t.qopt))
         return kReject;
     // centre c = p1 + (v_y|u|^2 - u_y|v|^2, u_x|v|^2 - v_x|u|^2) / (2D)
-    const float inv2d = 0.5f / D;
+    const float inv2d = 0.5f * approx_rcp(D);
     t.cpx = det2(t.vy, t.uy, t.vv, t.uu) * inv2d;
     t.cpy = det2(t.ux, t.vx, t.uu, t.vv) * inv2d;
     t.cx = p1.x + t.cpx;
     t.cy = p1.y + t.cpy;
     t.R = sq * fabsf(inv2d);
     t.inv2r = fabsf(D) * rq;
-    t.cn = sqrtf(fmaf(t.cx, t.cx, t.cy * t.cy));
+    t.cn = approx_sqrt(fmaf(t.cx, t.cx, t.cy * t.cy));
     // |c| - R = (|c|^2 - R^2) / (|c| + R), |c|^2 - R^2 = |p1|^2 + 2 p1.(c - p1)
     const float power = fmaf(p1.x, p1.x, p1.y * p1.y) + 2.0f * fmaf(p1.x, t.cpx, p1.y * t.cpy);
-    const float dist = power / (t.cn + t.R);
+    const float dist = power * approx_rcp(t.cn + t.R);
     t.sgn = D > 0.0f ? 1.0f : -1.0f;
     t.d0 = t.sgn * dist;
     if (!in_range_f32(C, 2, t.d0))
@@ -309,22 +323,10 @@ __device__ __forceinline__ int fit_transverse(const float4 &p1, const float4 &p2
     if (!(t.cn > 0.0f) || !(t.R < 3.0e37f))
         return kNeedFp64;
     // perigee P = c (|c| - R) / |c|
-    const float f = dist / t.cn;
+    const float f = dist * approx_rcp(t.cn);
     t.px = t.cx * f;
     t.py = t.cy * f;
     return kPass;
-}
-
-// Square root and reciprocal through the MUFU approximations (relative error a few 1e-7):
-// used only inside the conservative bound below, whose margins are 1e-4.
-__device__ __forceinline__ float approx_sqrt(float x)
-{
-    return x * rsqrtf(fmaxf(x, 1e-30f));
-}
-__device__ __forceinline__ float approx_rcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ float2 approx_sqrt(float2 x)
-{
-    return vmul(x, make_float2(rsqrtf(fmaxf(x.x, 1e-30f)), rsqrtf(fmaxf(x.y, 1e-30f))));
 }
 
 // arcsin(x) / x through the x^6 term of its series: 1 + x^2/6 + 3x^4/40 + 5x^6/112.  The
@@ -346,12 +348,9 @@ __device__ __forceinline__ bool in_range_loose(const FitConst &C, int k, float p
     return p >= C.lo[k] - m && p < C.hi[k] + m;
 }
 
-// The transverse fit of fit_transverse evaluated for the conservative pre-test: the same
-// formulas with the MUFU square root and reciprocal (a few 1e-7 relative error per
-// operation instead of IEEE rounding) and widened q/pT and d0 range tests, so it passes
-// every triplet that fit_transverse passes.  The FP64 trigger is computed exactly as there.
-// The perigee it returns is within |P| * 1e-6 of the exact one (P = c * dist / |c| with
-// |P| = dist), far inside the margins of z_may_accept.
+// The transverse fit of fit_transverse for the pre-test: the same arithmetic with the q/pT
+// and d0 range tests widened by 1e-4, so it passes every triplet that fit_transverse
+// passes.  The FP64 trigger is computed exactly as there.
 __device__ __forceinline__ int fit_transverse_bound(const float4 &p1, const float4 &p2,
                                                     const float4 &p3, const FitConst &C, Trans &t)
 {
@@ -508,13 +507,13 @@ __device__ __forceinline__ int fit_longitudinal(const float4 &p1, const float4 &
                                                 const float4 &p3, const Trans &t,
                                                 const FitConst &C, float &cot, float &z0)
 {
-    const float rcn = 1.0f / t.cn;
+    const float rcn = approx_rcp(t.cn);
     const float ax = -t.R * t.cx * rcn, ay = -t.R * t.cy * rcn;          // P - c
     const float b0x = -t.cpx, b0y = -t.cpy;                              // p1 - c
     const float dx0 = p1.x - t.px, dy0 = p1.y - t.py;
-    const float ch0 = sqrtf(fmaf(dx0, dx0, dy0 * dy0));
+    const float ch0 = approx_sqrt(fmaf(dx0, dx0, dy0 * dy0));
     const float sx = ax + b0x, sy = ay + b0y;
-    const float th0 = central_angle(ch0, sqrtf(fmaf(sx, sx, sy * sy)), t.inv2r);
+    const float th0 = central_angle(ch0, approx_sqrt(fmaf(sx, sx, sy * sy)), t.inv2r);
     const float s0 = (t.sgn * det2(dx0, dy0, t.cx, t.cy) >= 0.0f) ? t.R * th0 : -t.R * th0;
     const float turn = 6.2831853f * t.R;
     // hits 2 and 3 as a pair (.x, .y)
@@ -524,13 +523,14 @@ __device__ __forceinline__ int fit_longitudinal(const float4 &p1, const float4 &
     // (p1 - c) + (p_k - c) = 2 b + e for the complementary (long-chord) form
     const float2 qx = vfma(bc<float2>(2.0f), bc<float2>(b0x), ex);
     const float2 qy = vfma(bc<float2>(2.0f), bc<float2>(b0y), ey);
-    const float2 psi = central_angle(vsqrt(ee), vsqrt(vfma(qx, qx, vmul(qy, qy))), t.inv2r);
+    const float2 psi =
+        central_angle(approx_sqrt(ee), approx_sqrt(vfma(qx, qx, vmul(qy, qy))), t.inv2r);
     const float2 d = vsel(vge(vmul(bc<float2>(t.sgn), cr), bc<float2>(0.0f)),
                           vmul(bc<float2>(t.R), psi), vmul(bc<float2>(-t.R), psi));
     // crude s_k (good to a fraction of pi R): chord (1 + x^2/6) with its sign
     const float2 dx = vsub(make_float2(p2.x, p3.x), bc<float2>(t.px));
     const float2 dy = vsub(make_float2(p2.y, p3.y), bc<float2>(t.py));
-    const float2 ch = vsqrt(vfma(dx, dx, vmul(dy, dy)));
+    const float2 ch = approx_sqrt(vfma(dx, dx, vmul(dy, dy)));
     const float2 xk = vmul(ch, bc<float2>(t.inv2r));
     const float2 mag = vmul(ch, vfma(vmul(xk, xk), bc<float2>(1.0f / 6.0f), bc<float2>(1.0f)));
     const float2 crude =
@@ -553,7 +553,7 @@ __device__ __forceinline__ int fit_longitudinal(const float4 &p1, const float4 &
     const float ssz = fmaf(a0, p1.z - zbar, fmaf(a1, p2.z - zbar, a2 * (p3.z - zbar)));
     if (!(sss > 0.0f))
         return kNeedFp64;
-    cot = ssz / sss;
+    cot = approx_div(ssz, sss);
     z0 = fmaf(-cot, sbar, zbar);
     if (!in_range_f32(C, 3, cot) || !in_range_f32(C, 4, z0))
         return kReject;
