@@ -596,7 +596,9 @@ LAUNCHES_PER_CALL = 1 + 1 + 1 + 3 + 9 + 1 + 1 + 1 + 1 + 1
 VOTE_TRAFFIC = {"workload": "barrel10_500trk",
                 "sources_sha256": "eee6430b476e2a3ad60cd5f5af4b5c6c00c1684c19f0f69b67a510746f6da6cd",
                 "records": [{"tile_i": 8, "tile_j": 16, "vote_level": 4,
-                             "bytes": 1.11732864e9 + 3.241699072e9}]}
+                             "bytes": 1.11732864e9 + 3.241699072e9},
+                            {"tile_i": 16, "tile_j": 8, "vote_level": 4,
+                             "bytes": 1.115576832e9 + 3.240372736e9}]}
 VOTE_SOURCES = ["trk_common.cuh", "trk_vote_kernel.cuh", "trk_vote.cu", "trk_vote_l2.cu",
                 "trk_vote_l3.cu", "trk_vote_l4.cu"]
 
