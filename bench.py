@@ -594,7 +594,7 @@ LAUNCHES_PER_CALL = 1 + 1 + 1 + 3 + 9 + 1 + 1 + 1 + 1 + 1
 # only while the vote-kernel sources hash to the recorded digest, and the traffic is
 # reported as null for a tuning without a record.
 VOTE_TRAFFIC = {"workload": "barrel10_500trk",
-                "sources_sha256": "eee6430b476e2a3ad60cd5f5af4b5c6c00c1684c19f0f69b67a510746f6da6cd",
+                "sources_sha256": "708aa24aca5c591c2ba8810a343156a6f06e5b88d6fea6b81552a4ccb64eba04",
                 "records": [{"tile_i": 8, "tile_j": 16, "vote_level": 4,
                              "bytes": 1.11732864e9 + 3.241699072e9},
                             {"tile_i": 16, "tile_j": 8, "vote_level": 4,

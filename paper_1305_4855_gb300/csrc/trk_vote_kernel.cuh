@@ -8,7 +8,7 @@
 //   A  curvature prefilter (14 FP32 ops): a superset test of the q/pT range;
 //   B  the transverse pre-fit and the conservative longitudinal bound (superset tests of
 //      the q/pT, d0, cot and z0 ranges);
-//   C  the exact FP32 fit, phi0, the five bin indices, the histogram atomic and the
+//   C  the FP32 fit itself, phi0, the five bin indices, the histogram atomic and the
 //      vote-list record.
 // Between stages the surviving (pair, hit) items are compacted into per-warp ring
 // queues in shared memory so that B and C run with all 32 lanes busy.  Fits that the
