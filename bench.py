@@ -46,6 +46,13 @@ BATCH_WORKLOAD = "barrel10_batch256"
 OPS_PER_TRIPLET = 14
 OPS_PER_FIT = 80 + 197
 OPS_PER_EXACT = 65 + 146 + 31
+# The method's own work, independent of how the kernel prunes (the roofline's `achieved`):
+# every enumerated triplet needs the determinant, the three squared distances and the
+# curvature comparison before it can be rejected (the 14 above) plus the reciprocal and
+# the products of the q/pT range test, about 31 operations; every accepted triplet needs
+# the whole exact fit, phi0 and the five bins, the 242 of the exact path above.
+METHOD_OPS_PER_TRIPLET = 31
+METHOD_OPS_PER_VOTE = 65 + 146 + 31
 # Of those, the operations that go to the special-function (MUFU) pipe, the co-bound
 # (16 per SM per clock): square roots, reciprocal square roots, reciprocals, divisions,
 # arcsines and arctangents.
@@ -334,9 +341,14 @@ def main():
     sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
     # FP32 lane-operation peak: 128 FP32 lanes per SM per clock
     alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12
-    alg_ops = (OPS_PER_TRIPLET * stats["n_triplets"] + OPS_PER_FIT * stats["n_fit"] +
-               OPS_PER_EXACT * stats["n_exact"]) / 1e12
-    achieved = alg_ops / (vote_ms / 1000.0) if vote_ms else None
+    kernel_ops = (OPS_PER_TRIPLET * stats["n_triplets"] + OPS_PER_FIT * stats["n_fit"] +
+                  OPS_PER_EXACT * stats["n_exact"]) / 1e12
+    method_ops = (METHOD_OPS_PER_TRIPLET * stats["n_triplets"] +
+                  METHOD_OPS_PER_VOTE * stats["n_votes"]) / 1e12
+    achieved = method_ops / (vote_ms / 1000.0) if vote_ms else None
+    kernel_rate = kernel_ops / (vote_ms / 1000.0) if vote_ms else None
+    hbm_peak = peaks.get("hbm_gbs")
+    nbins = int(rec.lib.trk_histogram_size(rec.h))
     mufu_peak = sm_count * 16 * sm_mhz * 1e6 / 1e12
     mufu_ops = (MUFU_PER_FIT * stats["n_fit"] + MUFU_PER_EXACT * stats["n_exact"]) / 1e12
     mufu = mufu_ops / (vote_ms / 1000.0) if vote_ms else None
@@ -357,9 +369,15 @@ def main():
                      "traffic": vote_traffic(args.workload, tuning), "vote_kernel_ms": vote_ms,
                      "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (median SM clock under load)"
                                    % (sm_count, sm_mhz),
-                     "achieved_basis": "%d FP32 ops per enumerated triplet + %d per fit + %d per "
-                                       "exact fit (vote kernel stats of the call)"
-                                       % (OPS_PER_TRIPLET, OPS_PER_FIT, OPS_PER_EXACT),
+                     "achieved_basis": "the method's work: %d FP32 ops per enumerated triplet + "
+                                       "%d per accepted triplet (vote kernel stats of the call)"
+                                       % (METHOD_OPS_PER_TRIPLET, METHOD_OPS_PER_VOTE),
+                     "peak_source": "derived (SM count x lanes x sampled clock)",
+                     "issue_frac": (kernel_rate / alu_peak) if kernel_rate else None,
+                     "issue_basis": "the operations the kernel executes by design, pruning "
+                                    "included: %d per enumerated triplet + %d per curvature "
+                                    "survivor + %d per exact fit"
+                                    % (OPS_PER_TRIPLET, OPS_PER_FIT, OPS_PER_EXACT),
                      "mufu": {"achieved": mufu, "peak": mufu_peak, "unit": "T ops/s",
                               "frac": (mufu / mufu_peak) if mufu else None,
                               "basis": "%d special-function ops per fit + %d per exact fit; "
@@ -368,9 +386,24 @@ def main():
         "e2e": {"value": world * args.steps / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "stage_ms": stage_ms,
+        "hbm_rooflines": {
+            "peaks": {"kernels": "k_peak_pass1, k_peak_pass2, k_peak_ties (+ bitmap clears)",
+                      "bytes": 4 * nbins, "ms": stage_ms.get("peaks"),
+                      "achieved_gbs": (4 * nbins / (stage_ms["peaks"] / 1000.0) / 1e9)
+                      if stage_ms.get("peaks") else None,
+                      "peak_gbs": hbm_peak, "peak_source": "measured (MEASURED_PEAKS.json)",
+                      "basis": "one read of the event's dense histogram (4 B per bin)"},
+            "assign": {"kernels": "k_assign_fill, k_cand_hits, scans, k_compact",
+                       "bytes": 4 * stats["n_votes"], "ms": stage_ms.get("assign"),
+                       "achieved_gbs": (4 * stats["n_votes"] / (stage_ms["assign"] / 1000.0) / 1e9)
+                       if stage_ms.get("assign") else None,
+                       "peak_gbs": hbm_peak, "peak_source": "measured (MEASURED_PEAKS.json)",
+                       "basis": "one read of each vote's bin (4 B per vote)"}},
         "clocks": clocks,
         "gpu_launches": args.steps * (LAUNCHES_PER_CALL + int(args.with_fit)),
     }
+    for r in line["hbm_rooflines"].values():
+        r["frac"] = (r["achieved_gbs"] / r["peak_gbs"]) if r["achieved_gbs"] and r["peak_gbs"] else None
     rec.close()
     if not args.no_variants:
         line["variants"] = run_variants(args, local)

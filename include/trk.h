@@ -16,7 +16,11 @@
  * clockwise seen from +z, so q = -sign(D) with D = (p2 - p1) x (p3 - p1) in the
  * transverse plane (hits in layer order a, b, c); perigee P = closest point of the
  * circle to the origin, phi0 = direction of motion at P in [-pi, pi),
- * d0 = -P_x sin(phi0) + P_y cos(phi0); s_k = 2R asin(|p_k - P| / 2R);
+ * d0 = -P_x sin(phi0) + P_y cos(phi0); s_k = +-2R asin(|p_k - P| / 2R), the signed path
+ * length from P: + for a hit after P in the direction of motion ((p_k - P) . (cos phi0,
+ * sin phi0) >= 0), - for one before it, so that z = z0 + s cot(theta) holds on both sides
+ * of the perigee (a hit at the point opposite P, where the sign is undefined, makes the
+ * triplet edge-ambiguous); on a straight line (D == 0) s_k = +-|p_k - P|;
  * (cot(theta), z0) = unweighted least-squares line z = z0 + s cot(theta) over the three
  * hits; bin index floor((p - lo) / ((hi - lo)/n)), a triplet votes iff all five
  * parameters are in range, periodic dimensions are wrapped first; bins are numbered
@@ -101,10 +105,7 @@ typedef struct trk_options {
     int32_t k_chunk;                        /* outer-layer hits staged per shared chunk */
     int32_t blocks_per_sm;                  /* persistent vote blocks per SM (0: auto) */
     int32_t use_graph;                      /* capture each call shape in a CUDA graph (the
-                                               capture runs in the calling thread; do not
-                                               create or destroy handles in other threads
-                                               meanwhile: trk_destroy synchronises the
-                                               device) */
+                                               capture runs in the calling thread) */
     int32_t vote_level;                     /* vote kernel occupancy: 2, 3 or 4 blocks of 256
                                                threads per SM (0: 3) */
     int32_t fit_candidates;                 /* 1: fit a helix to every candidate's hits in
@@ -126,7 +127,7 @@ typedef struct trk_candidate {
  *
  * Paper Sec. 8 (with Fig. 6): the candidates found in the parameter space are then fitted
  * to their hits; the paper times such a fit but does not define it.  The fit here, in
- * FP64 on the device, one warp per candidate, hits in the candidate's (sorted) order:
+ * FP64 on the device, one thread per candidate, hits in the candidate's (sorted) order:
  *   1. algebraic circle fit of all the candidate's hits: (a, b, c) minimising
  *      sum (u^2 + v^2 + a u + b v + c)^2, (u, v) = (x, y) - centroid, through the 3 x 3
  *      normal equations; centre = centroid - (a, b)/2, R^2 = a^2/4 + b^2/4 - c;
@@ -196,11 +197,20 @@ typedef struct trk_ctx trk_ctx;
 void trk_options_default(trk_options *opt, int32_t max_events, int64_t max_hits);
 
 /* Create a handle: validates geometry and binning, copies them to the device and
- * allocates every pool.  *out receives the handle (NULL on failure). */
+ * allocates every pool.  *out receives the handle (NULL on failure).
+ * Paper Sec. 8: the event, the parameter space and the peak detection are resident on the
+ * GPU; the handle holds the geometry, the binned parameter space (Sec. 7, Fig. 3) and
+ * every buffer of the steps below, so that no call allocates. */
 int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk_binning *binning,
                const trk_options *options /* nullable: defaults for 1 event */);
 
-/* Reconstruct n_events events.  hits: DEVICE pointer to n_hits trk_hit; event_offsets:
+/* Reconstruct n_events events: paper Sec. 7 and Fig. 3 (every hit combination votes into
+ * the binned parameter space; local maxima are track candidates) with Sec. 8's curved
+ * displaced tracks (circle by centre and radius, no beam-spot constraint) and Sec. 8's
+ * hand-over of each candidate's hits to a fit.  Steps: pack the hits per layer, fit and
+ * bin every triplet of every listed layer triple, vote, find the candidate bins, collect
+ * each candidate's hits.
+ * hits: DEVICE pointer to n_hits trk_hit; event_offsets:
  * DEVICE pointer to n_events + 1 int64, event e owning hits [off[e], off[e+1]).  Runs on
  * `stream` (a cudaStream_t, NULL = the legacy default stream) and returns after the
  * per-event counts reached the host (the call's only synchronisation).  Returns TRK_OK,
@@ -211,12 +221,15 @@ int trk_reconstruct(trk_ctx *h, const trk_hit *hits, int64_t n_hits,
 
 /* Same, from HOST buffers (any host memory): copies the hits in, reconstructs and copies
  * the candidates and hit ids back to library-owned pinned host memory (out->h_cand,
- * out->h_hit_ids).  The end-to-end path of a caller whose events live in host memory. */
+ * out->h_hit_ids).  The end-to-end path of a caller whose events live in host memory
+ * (paper Sec. 8: the event is transferred to the GPU, processed there, and the candidates
+ * come back to the host for the fit). */
 int trk_reconstruct_host(trk_ctx *h, const trk_hit *hits, int64_t n_hits,
                          const int64_t *event_offsets, int32_t n_events,
                          trk_candidates *out, void *stream);
 
-/* Destroy a handle and free everything it owns.  NULL is accepted. */
+/* Destroy a handle and free everything it owns (the paper has no counterpart).  Waits for
+ * the handle's own work (its streams), not for the whole device.  NULL is accepted. */
 int trk_destroy(trk_ctx *h);
 
 /* Counters of the last call. */
@@ -285,7 +298,9 @@ typedef struct trk_served_event {
     int64_t n_hit_ids;
 } trk_served_event;
 
-/* Create a server of n_lanes (1..16) lanes; each lane allocates one trk handle with
+/* Paper Sec. 8 for every call below: the filter unit processes a stream of events, and
+ * the next event's transfer and processing overlap the current one's.
+ * Create a server of n_lanes (1..16) lanes; each lane allocates one trk handle with
  * lane_options.  fit_candidates is ignored (served events return candidates and hits), and
  * so is use_graph: lanes launch their kernels directly.  A lane runs in its own thread, and
  * while a stream of the process is capturing a CUDA graph, device-wide synchronisation
@@ -330,11 +345,14 @@ int trk_server_destroy(trk_server *s);
  * process exits.
  *
  * hist: DEVICE int32, n_events dense histograms of the binning's size, row-major (as
- * trk_get_histogram writes them); cand_bits: DEVICE uint32, n_events x ceil(bins / 32)
- * words, bit b of event e set iff bin b is a candidate; both owned by the caller.  Runs on
+ * trk_get_histogram writes them), 4-byte aligned (any int32 pointer; 16-byte alignment
+ * lets the kernels use wider loads); cand_bits: DEVICE uint32, n_events x ceil(bins / 32)
+ * words, 4-byte aligned, bit b of event e set iff bin b is a candidate; both owned by the
+ * caller.  Runs on
  * `stream` (a cudaStream_t; NULL = legacy default stream), asynchronously.
- * Returns TRK_ERR_INVALID (nothing launched) for null pointers, n_events < 1, an invalid
- * binning, or more than TRK_NOALLOC_MAX_BINS bins; TRK_ERR_CUDA on a launch failure.
+ * Returns TRK_ERR_INVALID (nothing launched) for null or misaligned pointers,
+ * n_events < 1, an invalid binning, or more than TRK_NOALLOC_MAX_BINS bins; TRK_ERR_CUDA on
+ * a launch failure.
  * trk_last_error(NULL) gives the reason.
  *
  * The first call on a device sets that device up (looks up the static array's device
@@ -343,7 +361,8 @@ int trk_server_destroy(trk_server *s);
  * the last call's contents (each call clears what it needs cleared -- its list counter
  * and the caller's cand_bits -- and writes every other entry before reading it); calls
  * whose work overlaps on the GPU (other streams, other threads) race on them and must be
- * serialized by the caller. */
+ * serialized by the caller.  The device addresses are kept for the life of the process:
+ * do not call this function after cudaDeviceReset. */
 int trk_find_peaks_noalloc(const int32_t *hist, int32_t n_events, const trk_binning *binning,
                            uint32_t *cand_bits, void *stream);
 

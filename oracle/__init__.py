@@ -14,5 +14,5 @@ the CUDA path produced as an input.
                       (numpy, FP64).
 """
 from .core import OracleSetup, enumerate_batch, fit_list, fit_tracks, max_threads  # noqa: F401
-from .reconstruct import (histogram, neighbour_offsets, peaks, assign_hits,  # noqa: F401
+from .reconstruct import (histogram, neighbour_offsets, peaks, assign_hits, bin_centres,  # noqa: F401
                           reconstruct)

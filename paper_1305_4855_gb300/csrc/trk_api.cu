@@ -6,6 +6,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <vector>
 
 #include "trk_common.cuh"
 
@@ -29,7 +30,7 @@ size_t peak_pass1_smem(const FitConst &C, int td);
 cudaError_t launch_peaks(const int32_t *hist, int32_t *m3, const FitConst &C, int g0, int G,
                          int td, int threshold, const int32_t *status,
                          unsigned long long *ties, unsigned long long *n_ties, int64_t tie_cap,
-                         int n_sm, cudaStream_t s);
+                         int n_sm, cudaStream_t s, bool vec_ok);
 cudaError_t launch_peak_ties(const int32_t *hist, const FitConst &C,
                              const unsigned long long *ties, const unsigned long long *n_ties,
                              int64_t tie_cap, uint32_t *cbits, int64_t W, uint32_t *filter,
@@ -142,6 +143,7 @@ struct trk_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t ev_st[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stage boundaries
     cudaStream_t own_stream = nullptr;   // used when the caller passes the legacy stream
+    std::vector<cudaEvent_t> pending;    // recorded after asynchronous work on caller streams
     trk_stats stats;
     int last_n_events = 0;
     std::string err;
@@ -321,6 +323,29 @@ static void free_all(trk_ctx *h)
     for (cudaEvent_t &e : h->ev_st)
         if (e)
             cudaEventDestroy(e);
+    for (cudaEvent_t e : h->pending)
+        cudaEventDestroy(e);
+    h->pending.clear();
+}
+
+// Marks the end of asynchronous work the handle enqueued on a caller's stream, so that
+// trk_destroy can wait for exactly that work (events of finished work are reused).
+static cudaError_t note_async(trk_ctx *h, cudaStream_t s)
+{
+    cudaEvent_t ev = nullptr;
+    for (size_t i = 0; i < h->pending.size(); ++i)
+        if (cudaEventQuery(h->pending[i]) == cudaSuccess) {
+            ev = h->pending[i];
+            h->pending.erase(h->pending.begin() + (long)i);
+            break;
+        }
+    if (!ev) {
+        const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess)
+            return e;
+    }
+    h->pending.push_back(ev);
+    return cudaEventRecord(ev, s);
 }
 
 template <class T>
@@ -515,7 +540,13 @@ extern "C" int trk_destroy(trk_ctx *h)
     if (!h)
         return TRK_OK;
     cudaSetDevice(h->device);
-    cudaDeviceSynchronize();
+    // wait for the handle's own work only: its stream, and what its asynchronous entry
+    // points left on callers' streams (a device-wide synchronisation would be invalid while
+    // another thread of the process captures a graph, e.g. a server lane)
+    if (h->own_stream)
+        cudaStreamSynchronize(h->own_stream);
+    for (cudaEvent_t e : h->pending)
+        cudaEventSynchronize(e);
     free_all(h);
     delete h;
     return TRK_OK;
@@ -564,7 +595,8 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     for (int g0 = 0; g0 < n_events; g0 += h->group) {
         const int G = (n_events - g0) < h->group ? (n_events - g0) : h->group;
         TRK_CUDA(h, launch_peaks(h->d_hist, h->d_m3, h->C, g0, G, h->td, h->bin.threshold,
-                                 h->d_status, h->d_ties, &ctr->n_ties, h->tie_cap, h->n_sm, s));
+                                 h->d_status, h->d_ties, &ctr->n_ties, h->tie_cap, h->n_sm, s,
+                                 true));
     }
     TRK_CUDA(h, launch_peak_ties(h->d_hist, h->C, h->d_ties, &ctr->n_ties, h->tie_cap, h->d_cbits,
                                  h->W, h->d_filter, &ctr->overflow, h->n_sm, s));
@@ -819,6 +851,7 @@ extern "C" int trk_get_histogram(trk_ctx *h, int32_t event, int32_t *dst, void *
     TRK_CUDA(h, cudaMemcpyAsync(dst, h->d_hist + (size_t)event * h->nbins,
                                 sizeof(int32_t) * (size_t)h->nbins, cudaMemcpyDeviceToDevice,
                                 (cudaStream_t)stream));
+    TRK_CUDA(h, note_async(h, (cudaStream_t)stream));
     return TRK_OK;
 }
 
@@ -871,6 +904,7 @@ extern "C" int trk_fit_triplets(trk_ctx *h, const trk_hit *hits, int64_t n_hits,
     TRK_CUDA(h, cudaSetDevice(h->device));
     TRK_CUDA(h, launch_fit_triplets(hits, n_hits, ijk, n, h->C, params, bins, flags,
                                     (cudaStream_t)stream));
+    TRK_CUDA(h, note_async(h, (cudaStream_t)stream));
     return TRK_OK;
 }
 

@@ -20,7 +20,11 @@
 //     different streams, or from different host threads) race and corrupt each other's
 //     results; serialize them.  The arrays keep the last call's contents; each call writes
 //     every count it reads and clears the list counter (and the caller's candidate bits)
-//     itself before use.
+//     itself before use;
+//   * the arrays' device addresses are looked up once per device and kept for the life of
+//     the process: after cudaDeviceReset the entry point must not be called again.
+// Several small histograms share one pass of the kernels (as many as fit in the arrays, at
+// most kMaxGroup); the bins the tie pass reads carry the event index.
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -32,7 +36,7 @@ size_t peak_pass1_smem(const FitConst &C, int td);
 cudaError_t launch_peaks(const int32_t *hist, int32_t *m3, const FitConst &C, int g0, int G,
                          int td, int threshold, const int32_t *status,
                          unsigned long long *ties, unsigned long long *n_ties, int64_t tie_cap,
-                         int n_sm, cudaStream_t s);
+                         int n_sm, cudaStream_t s, bool vec_ok);
 cudaError_t launch_peak_ties(const int32_t *hist, const FitConst &C,
                              const unsigned long long *ties, const unsigned long long *n_ties,
                              int64_t tie_cap, uint32_t *cbits, int64_t W, uint32_t *filter,
@@ -50,7 +54,8 @@ static __device__ __align__(256) int32_t g_peak_scratch[TRK_NOALLOC_MAX_BINS];
 static __device__ __align__(256) unsigned long long g_peak_ties[TRK_NOALLOC_MAX_BINS];
 static __device__ __align__(256) unsigned long long g_peak_counters[2];
 // Per-event status read by the peak kernels: always zero (never written).
-static __device__ __align__(256) int32_t g_zero_status[1];
+constexpr int kMaxGroup = 256;
+static __device__ __align__(256) int32_t g_zero_status[kMaxGroup];
 
 namespace {
 
@@ -126,6 +131,8 @@ extern "C" int trk_find_peaks_noalloc(const int32_t *hist, int32_t n_events,
 {
     if (!hist || !binning || !cand_bits || n_events < 1)
         return noalloc_fail(TRK_ERR_INVALID, "null pointer or n_events < 1");
+    if (((uintptr_t)hist & 3) != 0 || ((uintptr_t)cand_bits & 3) != 0)
+        return noalloc_fail(TRK_ERR_INVALID, "hist and cand_bits must be 4-byte aligned");
     double nb = 1.0;
     for (int k = 0; k < 5; ++k) {
         if (binning->n[k] < 1 || !(binning->lo[k] < binning->hi[k]))
@@ -171,16 +178,22 @@ extern "C" int trk_find_peaks_noalloc(const int32_t *hist, int32_t n_events,
     if (e != cudaSuccess)
         return noalloc_fail(TRK_ERR_CUDA, std::string("clearing cand_bits: ") +
                                               cudaGetErrorString(e));
-    for (int ev = 0; ev < n_events; ++ev) {
+    // events per pass: their box maxima must fit in the scratch array
+    int group = (int)(TRK_NOALLOC_MAX_BINS / C.nbins);
+    group = group < 1 ? 1 : (group > kMaxGroup ? kMaxGroup : group);
+    for (int g0 = 0; g0 < n_events; g0 += group) {
+        const int G = n_events - g0 < group ? n_events - g0 : group;
+        const int32_t *hg = hist + (size_t)g0 * C.nbins;
+        // the 16-byte loads of pass 2 need a 16-byte aligned histogram
+        const bool vec_ok = ((uintptr_t)hg & 15) == 0;
         e = cudaMemsetAsync(d->counters, 0, 2 * sizeof(unsigned long long), s);
         if (e == cudaSuccess)
-            e = launch_peaks(hist + (size_t)ev * C.nbins, d->scratch, C, 0, 1, td,
-                             binning->threshold, d->zero, d->ties, d->counters,
-                             TRK_NOALLOC_MAX_BINS, d->n_sm, s);
+            e = launch_peaks(hg, d->scratch, C, 0, G, td, binning->threshold, d->zero, d->ties,
+                             d->counters, TRK_NOALLOC_MAX_BINS, d->n_sm, s, vec_ok);
         if (e == cudaSuccess)
-            e = launch_peak_ties(hist + (size_t)ev * C.nbins, C, d->ties, d->counters,
-                                 TRK_NOALLOC_MAX_BINS, cand_bits + (size_t)ev * W, W,
-                                 nullptr, d->counters + 1, d->n_sm, s);
+            e = launch_peak_ties(hg, C, d->ties, d->counters, TRK_NOALLOC_MAX_BINS,
+                                 cand_bits + (size_t)g0 * W, W, nullptr, d->counters + 1,
+                                 d->n_sm, s);
         if (e != cudaSuccess)
             return noalloc_fail(TRK_ERR_CUDA, std::string("peak kernels: ") +
                                                   cudaGetErrorString(e));

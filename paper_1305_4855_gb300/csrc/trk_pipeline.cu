@@ -857,16 +857,17 @@ size_t peak_pass1_smem(const FitConst &C, int td)
 
 // Peak passes 1 and 2 for events [g0, g0 + G): lists the bins whose count reaches the
 // box maximum (and the threshold).
+// vec_ok: hist is 16-byte aligned, so that pass 2 may read it with 16-byte loads.
 cudaError_t launch_peaks(const int32_t *hist, int32_t *m3, const FitConst &C, int g0, int G,
                          int td, int threshold, const int32_t *status,
                          unsigned long long *ties, unsigned long long *n_ties, int64_t tie_cap,
-                         int n_sm, cudaStream_t s)
+                         int n_sm, cudaStream_t s, bool vec_ok)
 {
     const size_t sm = peak_pass1_smem(C, td);
     const int nslab = (C.n[2] + td - 1) / td;
     const int64_t grid1 = (int64_t)G * C.n[0] * C.n[1] * nslab;
     k_peak_pass1<<<(unsigned)grid1, kPeakThreads, sm, s>>>(hist, m3, C, g0, td, status);
-    const bool vec = (C.stride[1] % 4) == 0;
+    const bool vec = vec_ok && (C.stride[1] % 4) == 0;
     const int64_t threads = (int64_t)G * C.n[1] * C.stride[1] / (vec ? 4 : 1);
     int64_t grid2 = (threads + kPeakThreads - 1) / kPeakThreads;
     const int64_t cap2 = (int64_t)n_sm * 32;

@@ -11,6 +11,11 @@ test: it imports neither the oracle nor the CUDA library.
       a hit the particle passes before reaching the perigee).
   peak_rule.json -- hand-built 5-D histograms for the local-maximum rule (Sec. 7 and
       Fig. 3 of the paper: candidates are local maxima of the parameter space).
+  bin_centres.json -- candidate parameters (bin centres) of chosen bins, worked out by
+      hand from the bin widths and the row-major numbering.
+  track_fit_chi2.json -- the candidate fit (Sec. 8 and Fig. 6: candidates are fitted to
+      their hits) on hit lists whose fitted circle and line are fixed by symmetry or by
+      construction, with their residual sums.
 
 Run: python tests/golden/make_fixtures.py
 """
@@ -120,9 +125,108 @@ def peak_rule():
                 periodic=[True, False, False, False, False], cases=pk)
 
 
+def bin_centres():
+    """Candidate parameters are bin centres, lo + (idx + 1/2)(hi - lo)/n per dimension, with
+    the bin number row-major (phi0 slowest).  Each expected value is worked out below from
+    the widths, not computed from that expression."""
+    pi = math.pi
+    # 64 x 64 x 32 x 32 x 16 over (-pi, pi), (-2, 2), (-50, 50), (-5.5, 5.5), (-30, 30):
+    # widths pi/32, 1/16, 3.125, 0.34375, 3.75; strides 1048576, 16384, 512, 16, 1
+    big = dict(lo=[-pi, -2.0, -50.0, -5.5, -30.0], hi=[pi, 2.0, 50.0, 5.5, 30.0],
+               n=[64, 64, 32, 32, 16], periodic=[True, False, False, False, False])
+    # 5 x 7 x 3 x 9 x 1 over (-pi, pi), (-1, 1), (-3, 3), (-1.25, 1.25), (-20, 20):
+    # widths 2pi/5, 2/7, 2, 5/18, 40; strides 189, 27, 9, 1, 1
+    odd = dict(lo=[-pi, -1.0, -3.0, -1.25, -20.0], hi=[pi, 1.0, 3.0, 1.25, 20.0],
+               n=[5, 7, 3, 9, 1], periodic=[True, False, False, False, False])
+    cases = [
+        dict(name="lowest_bin", binning="big", bin=0,
+             expected=[-63.0 * pi / 64.0, -1.96875, -48.4375, -5.328125, -28.125],
+             why="every index 0: half a width above each lower edge (pi/64, 1/32, 1.5625, "
+                 "0.171875, 1.875)"),
+        dict(name="highest_bin", binning="big", bin=67108863,
+             expected=[63.0 * pi / 64.0, 1.96875, 48.4375, 5.328125, 28.125],
+             why="63*1048576 + 63*16384 + 31*512 + 31*16 + 15 = 67108863, the last bin: half a "
+                 "width below each upper edge"),
+        dict(name="phi0_wrap_row", binning="big", bin=66068495,
+             expected=[63.0 * pi / 64.0, -1.96875, 1.5625, -5.328125, 28.125],
+             why="63*1048576 + 0 + 16*512 + 0 + 15 = 66068495: the phi0 row next to the wrap, "
+                 "d0 index 16 is -50 + 16.5*3.125 = 1.5625"),
+        dict(name="middle_bin", binning="big", bin=34087176,
+             expected=[pi / 64.0, 0.03125, 1.5625, 0.171875, 1.875],
+             why="32*1048576 + 32*16384 + 16*512 + 16*16 + 8 = 34087176: the first bin above "
+                 "the middle of every dimension, half a width above zero"),
+        dict(name="odd_last_bin", binning="odd", bin=944,
+             expected=[0.8 * pi, 6.0 / 7.0, 2.0, 10.0 / 9.0, 0.0],
+             why="4*189 + 6*27 + 2*9 + 8 = 944 = 5*7*3*9 - 1: -pi + 4.5*2pi/5 = 0.8 pi, "
+                 "-1 + 6.5*2/7 = 6/7, -3 + 2.5*2 = 2, -1.25 + 8.5*5/18 = 10/9, single z0 bin "
+                 "centred on 0"),
+        dict(name="odd_centre_bin", binning="odd", bin=472,
+             expected=[0.0, 0.0, 0.0, 0.0, 0.0],
+             why="2*189 + 3*27 + 1*9 + 4 = 472: the middle bin of each odd count, centred on "
+                 "zero in every dimension"),
+    ]
+    return dict(source="hand-worked bin centres, see make_fixtures.py",
+                binnings=dict(big=big, odd=odd), cases=cases)
+
+
+def track_fit_chi2():
+    """Candidate-fit residual sums (the fit's stated reading: algebraic circle fit, one hit
+    per layer, signed arcs, least-squares line) on hit lists whose fitted circle and line
+    are fixed by symmetry or by construction, so that chi2_rphi and chi2_rz are known."""
+    cases = []
+    # A: centre (0, 50); hits at 0, 90, 180, 270 degrees about it at distances 40.5, 39.5,
+    # 40.5, 39.5.  The set is symmetric under the point reflection through the centre, so
+    # the algebraic fit's centre is (0, 50) and its R^2 is the mean squared distance,
+    # (40.5^2 + 39.5^2)/2 = 1600.25.  Radial residuals 40.5 - R', 39.5 - R'.  z constant:
+    # cot = 0, z0 = 3, chi2_rz = 0.
+    rp = math.sqrt(1600.25)
+    cases.append(dict(
+        name="symmetric_radial_residuals",
+        derivation="centrally symmetric about (0,50): fitted centre (0,50), R'^2 = 1600.25; "
+                   "counter-clockwise in layer order (negative charge); P = (0, 50 - R'), "
+                   "phi0 = 0, d0 = 50 - R'; chi2_rphi = 2(40.5 - R')^2 + 2(39.5 - R')^2",
+        b_tesla=B, hits=[[0.0, 9.5, 3.0], [39.5, 50.0, 3.0], [0.0, 90.5, 3.0], [-39.5, 50.0, 3.0]],
+        layers=[0, 1, 2, 3], used=[1, 1, 1, 1],
+        expected=[0.0, -1.0 / (K * B * rp), 50.0 - rp, 0.0, 3.0],
+        chi2=[2.0 * (40.5 - rp) ** 2 + 2.0 * (39.5 - rp) ** 2, 0.0]))
+    # B: four hits exactly on the circle centre (0, 50), radius 40 (3-4-5 triangles); the
+    # arcs from P = (0, 10) are 40 (theta + pi/2).  z = 1 + 0.5 s + r with
+    # r = 0.01 (s3 - s2, s1 - s3, s2 - s1, 0), orthogonal to (1,1,1,1) and to s, so the
+    # least-squares line is exactly z = 1 + 0.5 s and chi2_rz = sum r^2.
+    R = 40.0
+    th = [math.atan2(-32.0, 24.0), math.atan2(-24.0, 32.0), 0.0, math.atan2(32.0, 24.0)]
+    s = [R * (t + math.pi / 2.0) for t in th]
+    a = 0.01
+    r = [a * (s[2] - s[1]), a * (s[0] - s[2]), a * (s[1] - s[0]), 0.0]
+    pts = [[24.0, 18.0], [32.0, 26.0], [40.0, 50.0], [24.0, 82.0]]
+    hits = [[p[0], p[1], 1.0 + 0.5 * sk + rk] for p, sk, rk in zip(pts, s, r)]
+    chi2_rz = sum(x * x for x in r)
+    cases.append(dict(
+        name="z_residuals_orthogonal_to_the_line",
+        derivation="hits on the circle centre (0,50), R = 40; P = (0,10), phi0 = 0, d0 = 10; "
+                   "z residuals orthogonal to 1 and s: the line is z = 1 + 0.5 s; "
+                   "chi2_rz = sum r_k^2, chi2_rphi = 0",
+        b_tesla=B, hits=hits, layers=[0, 1, 2, 3], used=[1, 1, 1, 1],
+        expected=[0.0, -1.0 / (K * B * R), 10.0, 0.5, 1.0], chi2=[0.0, chi2_rz]))
+    # C: B plus a second layer-1 hit far off the circle; it is dropped, and the sums run
+    # over the kept hits only, so chi2 equals B's.
+    hits_c = hits[:2] + [[32.0, 35.0, 0.0]] + hits[2:]
+    cases.append(dict(
+        name="dropped_duplicate_not_summed",
+        derivation="B with an extra layer-1 hit (32, 35), 4.7 cm inside the circle: the "
+                   "per-layer choice keeps (32, 26); the refit and both sums equal B's",
+        b_tesla=B, hits=hits_c, layers=[0, 1, 1, 2, 3], used=[1, 1, 0, 1, 1],
+        expected=[0.0, -1.0 / (K * B * R), 10.0, 0.5, 1.0], chi2=[0.0, chi2_rz]))
+    return dict(source="hand-derived candidate-fit sums, see make_fixtures.py", cases=cases)
+
+
 if __name__ == "__main__":
     with open(os.path.join(HERE, "hand_triplets.json"), "w") as f:
         json.dump(hand_triplets(), f, indent=1)
     with open(os.path.join(HERE, "peak_rule.json"), "w") as f:
         json.dump(peak_rule(), f, indent=1)
-    print("wrote hand_triplets.json, peak_rule.json")
+    with open(os.path.join(HERE, "bin_centres.json"), "w") as f:
+        json.dump(bin_centres(), f, indent=1)
+    with open(os.path.join(HERE, "track_fit_chi2.json"), "w") as f:
+        json.dump(track_fit_chi2(), f, indent=1)
+    print("wrote hand_triplets.json, peak_rule.json, bin_centres.json, track_fit_chi2.json")

@@ -4,6 +4,7 @@ Events of the batch workload's multiplicity mix (scaled down so the suite stays 
 arrive with random gaps, including bursts; each event's candidates and hit lists from the
 server must equal those of the same event reconstructed alone, whatever batch it shared.
 """
+import ctypes
 import time
 
 import numpy as np
@@ -82,4 +83,40 @@ def test_server_rejects_oversized_event(trk):
     with pytest.raises(trk.TrkError) as ex:
         srv.submit(big.packed())
     assert ex.value.code == trk.TRK_ERR_CAPACITY
+    srv.close()
+
+
+def test_handles_created_and_destroyed_while_the_server_runs(trk):
+    # handles with graph capture are created, used and destroyed in this thread while the
+    # server's lanes reconstruct in theirs: destruction waits for the handle's own work
+    # only, so neither side fails
+    cfg, evs = _events(12, seed=17)
+    srv = trk.Server(cfg, lane_events=4, lane_hits=8192, n_lanes=2, vote_capacity=1 << 25,
+                     cand_capacity=1 << 19, assign_capacity=1 << 23)
+    tickets = [srv.submit(e.packed()) for e in evs]
+    alone = []
+    for e in evs[:6]:
+        rec = trk.Reconstructor(cfg, max_events=1, max_hits=max(e.n_hits, 1),
+                                vote_capacity=1 << 24, cand_capacity=1 << 18,
+                                assign_capacity=1 << 22, use_graph=1)
+        hits = torch.from_numpy(e.packed()).cuda()
+        offs = torch.from_numpy(e.offsets).cuda()
+        res = rec.result(rec.reconstruct_device(hits, offs))
+        assert res.rc == 0, rec.error()
+        h = torch.empty(rec.lib.trk_histogram_size(rec.h), dtype=torch.int32, device="cuda")
+        # an asynchronous copy left pending when the handle is destroyed
+        assert rec.lib.trk_get_histogram(rec.h, 0, ctypes.c_void_p(h.data_ptr()),
+                                         ctypes.c_void_p(0)) == 0
+        alone.append(res.event(0))
+        rec.close()
+    for i, (t, e) in enumerate(zip(tickets, evs)):
+        info = srv.wait(t, timeout_s=120.0)
+        assert info is not None and info["status"] == 0 and info["rc"] == 0, info
+        cand, hits = srv.take(t, info)
+        if i < len(alone):
+            ca, ha = alone[i]
+            assert np.array_equal(cand["bin"], ca["bin"])
+            for x, y in zip(hits, ha):
+                assert np.array_equal(x, y)
+    assert srv.counts()["failed"] == 0
     srv.close()

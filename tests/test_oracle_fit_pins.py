@@ -173,3 +173,21 @@ def test_fit_tracks_matches_single_fits():
         assert r["status"][t] == f["status"]
         if f["status"] == 0:
             assert np.array_equal(r["par"][t], f["par"]) and np.array_equal(r["use"][t], f["use"])
+
+
+def test_golden_residual_sums():
+    # chi2_rphi and chi2_rz on hit lists whose fitted circle and line are known by
+    # symmetry or construction (tests/golden/track_fit_chi2.json): a residual that is not
+    # squared, or a sum over a dropped hit, changes them
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                    "track_fit_chi2.json")))
+    for c in g["cases"]:
+        f = fit_track_points(np.array(c["hits"]), np.array(c["layers"], dtype=np.int32),
+                             c["b_tesla"])
+        assert f["status"] == 0, c["name"]
+        assert np.array_equal(f["use"], np.array(c["used"], dtype=bool)), c["name"]
+        ok, d = _close(f["par"], np.array(c["expected"]), rel=1e-9, floor=1e-6)
+        assert ok, (c["name"], f["par"], c["expected"], d)
+        assert np.allclose(f["chi2"], c["chi2"], rtol=1e-9, atol=1e-12), (c["name"], f["chi2"], c["chi2"])

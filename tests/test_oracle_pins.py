@@ -459,3 +459,17 @@ def test_assign_hits_union():
     out = oracle.assign_hits(ijk, bins, np.array([5, 7]))
     assert out[0].tolist() == [0, 1, 2, 3, 4, 9]
     assert out[1].tolist() == [5, 6, 7]
+
+
+def test_golden_bin_centres():
+    # candidate parameters: hand-worked centres of chosen bins (lowest, highest, next to
+    # the phi0 wrap, middle; an odd binning with a single z0 bin)
+    g = json.load(open(os.path.join(GOLDEN, "bin_centres.json")))
+    for c in g["cases"]:
+        b = g["binnings"][c["binning"]]
+        setup = oracle.OracleSetup(
+            b_tesla=3.8, n_layers=3, triples=np.array([[0, 1, 2]], dtype=np.int32),
+            lo=np.array(b["lo"]), hi=np.array(b["hi"]), n=np.array(b["n"]),
+            periodic=np.array(b["periodic"]), threshold=1)
+        got = oracle.bin_centres(np.array([c["bin"]], dtype=np.int64), setup)[0]
+        assert np.allclose(got, c["expected"], rtol=0, atol=1e-12), (c["name"], got, c["expected"])

@@ -33,11 +33,7 @@ def _bits_to_bins(words: np.ndarray, nbins: int) -> np.ndarray:
     return np.nonzero(bits)[0].astype(np.int64)
 
 
-def test_noalloc_peaks_equal_reconstruct_candidates(trk):
-    cfg = ev.load_workload("barrel4_20trk")
-    # two different batches (2 events, then 1 event), one call each, in a row
-    batches = [ev.concat([ev.make_batch(cfg, seed=41), ev.make_batch(cfg, seed=42)]),
-               ev.make_batch(cfg, seed=43)]
+def _check_against_reconstruct(trk, cfg, batches, pad_ints=0):
     for batch in batches:
         rec = trk.Reconstructor(cfg, max_events=batch.n_events, max_hits=batch.n_hits,
                                 vote_capacity=1 << 20, cand_capacity=1 << 16,
@@ -48,10 +44,14 @@ def test_noalloc_peaks_equal_reconstruct_candidates(trk):
         assert res.rc == 0
         nbins = int(rec.lib.trk_histogram_size(rec.h))
         words = (nbins + 31) // 32
-        hist = torch.cat([rec.histogram(e) for e in range(batch.n_events)])
+        # pad_ints int32 in front: the histograms start 4 * pad_ints bytes past an aligned
+        # allocation (any int32 pointer is valid input)
+        hist = torch.cat([torch.zeros(pad_ints, dtype=torch.int32, device="cuda")] +
+                         [rec.histogram(e) for e in range(batch.n_events)])
         bits = torch.full((batch.n_events * words,), -1, dtype=torch.int32, device="cuda")
         stream = torch.cuda.current_stream().cuda_stream
-        rc = rec.lib.trk_find_peaks_noalloc(C.c_void_p(hist.data_ptr()), batch.n_events,
+        rc = rec.lib.trk_find_peaks_noalloc(C.c_void_p(hist.data_ptr() + 4 * pad_ints),
+                                            batch.n_events,
                                             C.byref(rec.bin), C.c_void_p(bits.data_ptr()),
                                             C.c_void_p(stream))
         assert rc == trk.TRK_OK, rec.lib.trk_last_error(None)
@@ -60,9 +60,44 @@ def test_noalloc_peaks_equal_reconstruct_candidates(trk):
         for e in range(batch.n_events):
             cand, _ = res.event(e)
             expect = np.sort(cand["bin"].astype(np.int64))
-            assert len(expect) > 10
+            assert len(expect) > 3
             assert np.array_equal(_bits_to_bins(got[e], nbins), expect)
         rec.close()
+
+
+def test_noalloc_peaks_equal_reconstruct_candidates(trk):
+    cfg = ev.load_workload("barrel4_20trk")
+    # two different batches (2 events, then 1 event), one call each, in a row
+    batches = [ev.concat([ev.make_batch(cfg, seed=41), ev.make_batch(cfg, seed=42)]),
+               ev.make_batch(cfg, seed=43)]
+    _check_against_reconstruct(trk, cfg, batches)
+
+
+def test_noalloc_unaligned_and_non_periodic(trk):
+    # histograms 4 bytes past a 16-byte boundary (narrower loads), then a binning whose
+    # phi0 does not wrap, with a d0 axis shorter than the filter's slab
+    cfg = ev.load_workload("barrel4_20trk")
+    _check_against_reconstruct(trk, cfg, [ev.make_batch(cfg, seed=44)], pad_ints=1)
+    _check_against_reconstruct(trk, cfg, [ev.make_batch(cfg, seed=45)], pad_ints=3)
+    flat = dict(cfg, binning=dict(cfg["binning"], periodic=[False] * 5,
+                                  n=[16, 16, 2, 16, 16]))
+    _check_against_reconstruct(trk, flat, [ev.concat([ev.make_batch(flat, seed=46),
+                                                      ev.make_batch(flat, seed=47)])])
+
+
+def test_noalloc_rejects_misaligned_pointers(trk):
+    cfg = ev.load_workload("barrel4_20trk")
+    binning = trk.binning_from_workload(cfg)
+    lib = trk.load_library()
+    buf = torch.zeros(1 << 20, dtype=torch.int32, device="cuda")
+    words = torch.zeros(1 << 16, dtype=torch.int32, device="cuda")
+    rc = lib.trk_find_peaks_noalloc(C.c_void_p(buf.data_ptr() + 2), 1, C.byref(binning),
+                                    C.c_void_p(words.data_ptr()), None)
+    assert rc == trk.TRK_ERR_INVALID
+    assert b"aligned" in lib.trk_last_error(None)
+    rc = lib.trk_find_peaks_noalloc(C.c_void_p(buf.data_ptr()), 1, C.byref(binning),
+                                    C.c_void_p(words.data_ptr() + 1), None)
+    assert rc == trk.TRK_ERR_INVALID
 
 
 def test_noalloc_rejects_oversized_histograms(trk):
