@@ -30,6 +30,14 @@ def _load():
         lib.orc_fit_tracks.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
                                        C.c_double, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p]
+        lib.orc_run_blocks.restype = C.c_int
+        lib.orc_run_blocks.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p,
+                                       C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p]
+        lib.orc_block_result_free.argtypes = [C.c_void_p]
+        lib.orc_block_peaks.restype = C.c_int64
+        lib.orc_block_peaks.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                        C.c_void_p, C.c_void_p, C.c_int64]
         _lib = lib
     return _lib
 
@@ -45,6 +53,19 @@ class _Result(C.Structure):
                 ("acc_bin", C.c_void_p), ("acc_amb", C.c_void_p), ("acc_par", C.c_void_p),
                 ("n_near", C.c_int64), ("near_event", C.c_void_p), ("near_ijk", C.c_void_p),
                 ("n_triplets", C.c_int64), ("n_degenerate", C.c_int64)]
+
+
+class _BlockResult(C.Structure):
+    _fields_ = [("n_keep", C.c_int64), ("keep_ijk", C.c_void_p), ("keep_bin", C.c_void_p),
+                ("n_flip", C.c_int64), ("flip_ijk", C.c_void_p), ("flip_bin", C.c_void_p),
+                ("flip_acc", C.c_void_p), ("n_triplets", C.c_int64), ("n_degenerate", C.c_int64)]
+
+
+def _arr(ptr, dtype, count):
+    if count == 0:
+        return np.zeros(0, dtype=dtype)
+    buf = (C.c_char * (count * np.dtype(dtype).itemsize)).from_address(ptr)
+    return np.frombuffer(buf, dtype=dtype).copy()
 
 
 @dataclass
@@ -209,3 +230,67 @@ def fit_track_points(xyz, layer, b_tesla: float, eps_rel: float = 1e-5) -> dict:
                            C.c_double(eps_rel), use.ctypes.data, par.ctypes.data,
                            chi2.ctypes.data, amb.ctypes.data)
     return dict(status=int(st), par=par, chi2=chi2, amb=int(amb[0]), use=use[:n].astype(bool))
+
+
+def enumerate_blocks(xyz, layer, setup: OracleSetup, count_blocks, keep_blocks, flip_blocks,
+                     n_threads: int = 0) -> dict:
+    """The definition over every triplet of ONE event, keeping only part of the output
+    (trk_oracle.c, orc_run_blocks).  A block is a (phi0 row, q/pT row) pair of bin indices.
+    count_blocks: list of (i0, i1) whose bins are counted (dense); keep_blocks: blocks whose
+    accepted triplets are listed; flip_blocks: blocks whose edge-ambiguous accepted triplets
+    are listed (near-accepted and antipode-ambiguous triplets are listed wherever they fall).
+    """
+    lib = _load()
+    hits = _hits_struct(xyz, layer)
+    n0, n1 = int(setup.n[0]), int(setup.n[1])
+    inner = int(setup.n[2] * setup.n[3] * setup.n[4])
+    slot = -np.ones(n0 * n1, dtype=np.int32)
+    for q, (i0, i1) in enumerate(count_blocks):
+        slot[i0 * n1 + i1] = q
+    keep = np.zeros(n0 * n1, dtype=np.uint8)
+    for i0, i1 in keep_blocks:
+        keep[i0 * n1 + i1] = 1
+    flip = np.zeros(n0 * n1, dtype=np.uint8)
+    for i0, i1 in flip_blocks:
+        flip[i0 * n1 + i1] = 1
+    counts = np.zeros(max(len(count_blocks), 1) * inner, dtype=np.int32)
+    offs = np.array([0, len(hits)], dtype=np.int64)
+    s, tri = setup._c()
+    res = _BlockResult()
+    rc = lib.orc_run_blocks(hits.ctypes.data, C.c_int64(len(hits)), offs.ctypes.data, 1,
+                            C.byref(s), C.c_int32(n_threads), slot.ctypes.data, keep.ctypes.data,
+                            flip.ctypes.data, counts.ctypes.data, C.byref(res))
+    if rc != 0:
+        raise ValueError("oracle: invalid input")
+    try:
+        out = dict(slot=slot, counts=counts.reshape(max(len(count_blocks), 1), inner),
+                   keep_ijk=_arr(res.keep_ijk, np.int32, 3 * res.n_keep).reshape(-1, 3),
+                   keep_bin=_arr(res.keep_bin, np.uint64, res.n_keep).astype(np.int64),
+                   flip_ijk=_arr(res.flip_ijk, np.int32, 3 * res.n_flip).reshape(-1, 3),
+                   flip_bin=_arr(res.flip_bin, np.uint64, res.n_flip).astype(np.int64),
+                   flip_acc=_arr(res.flip_acc, np.uint8, res.n_flip).astype(bool),
+                   n_triplets=int(res.n_triplets), n_degenerate=int(res.n_degenerate))
+    finally:
+        lib.orc_block_result_free(C.byref(res))
+    return out
+
+
+def block_peaks(blocks: dict, setup: OracleSetup, keep_blocks) -> tuple:
+    """Candidates (bins, votes) of the keep blocks from enumerate_blocks' counts, by the peak
+    rule in plain C (trk_oracle.c, orc_block_peaks)."""
+    lib = _load()
+    n0, n1 = int(setup.n[0]), int(setup.n[1])
+    keep = np.zeros(n0 * n1, dtype=np.uint8)
+    for i0, i1 in keep_blocks:
+        keep[i0 * n1 + i1] = 1
+    counts = np.ascontiguousarray(blocks["counts"], dtype=np.int32)
+    cap = int(len(keep_blocks) * counts.shape[1])
+    bins = np.zeros(max(cap, 1), dtype=np.uint64)
+    votes = np.zeros(max(cap, 1), dtype=np.int32)
+    s, tri = setup._c()
+    n = lib.orc_block_peaks(C.byref(s), blocks["slot"].ctypes.data, counts.ctypes.data,
+                            keep.ctypes.data, C.c_int32(setup.threshold), bins.ctypes.data,
+                            votes.ctypes.data, C.c_int64(cap))
+    if n < 0:
+        raise ValueError("oracle: a neighbour block of a keep block is not counted")
+    return bins[:n].astype(np.int64), votes[:n].astype(np.int64)

@@ -456,6 +456,266 @@ void orc_fit_list(const orc_hit *hits, const int32_t *ijk, int64_t n, const orc_
     }
 }
 
+/* ---------------------------------------------------------------------------------------
+ * The same definition restricted in its OUTPUT to blocks of the parameter space, for events
+ * whose accepted-triplet list does not fit in memory.  Every triplet of the event is fitted
+ * and binned exactly as in orc_run (same functions, same order within a work unit); only
+ * what is kept afterwards differs.  A block is one (phi0 row, q/pT row) pair of bin indices
+ * (i0, i1), holding the n2 * n3 * n4 bins that share them.  Per block:
+ *   count_slot[i0 * n1 + i1] >= 0: the block's votes are counted in
+ *       counts[slot * (n2 n3 n4) + (bin mod n2 n3 n4)];
+ *   keep_sel: accepted triplets voting in the block are listed (hit indices and bin);
+ *   flip_sel: accepted triplets voting in the block with a parameter within eps of a bin
+ *       edge are listed (for explaining FP32 bin flips).
+ * Rejected triplets whose out-of-range parameters all lie within eps of their range limits
+ * (near-accepted), and triplets with a hit at the point opposite the perigee, are listed
+ * wherever they fall.  One event per call.
+ * --------------------------------------------------------------------------------------- */
+typedef struct {
+    int64_t n_keep;
+    int32_t *keep_ijk;      /* [3 n_keep] input hit indices */
+    uint64_t *keep_bin;
+    int64_t n_flip;
+    int32_t *flip_ijk;      /* [3 n_flip] */
+    uint64_t *flip_bin;     /* the oracle's bin (accepted) or 0 (rejected) */
+    uint8_t *flip_acc;      /* 1 accepted by the oracle, 0 rejected */
+    int64_t n_triplets;
+    int64_t n_degenerate;
+} orc_block_result;
+
+typedef struct {
+    int64_t n, cap;
+    int32_t *ijk;
+    uint64_t *bin;
+    uint8_t *acc;
+} blk_buf;
+
+static void blk_push(blk_buf *b, int32_t i, int32_t j, int32_t k, uint64_t bin, int acc)
+{
+    if (b->n == b->cap) {
+        b->cap = b->cap ? 2 * b->cap : 64;
+        b->ijk = realloc(b->ijk, (size_t)b->cap * 3 * sizeof(int32_t));
+        b->bin = realloc(b->bin, (size_t)b->cap * sizeof(uint64_t));
+        b->acc = realloc(b->acc, (size_t)b->cap);
+    }
+    b->ijk[3 * b->n] = i;
+    b->ijk[3 * b->n + 1] = j;
+    b->ijk[3 * b->n + 2] = k;
+    b->bin[b->n] = bin;
+    b->acc[b->n] = (uint8_t)acc;
+    b->n++;
+}
+
+static void blk_flatten(blk_buf *bufs, int64_t n_units, int64_t *n_out, int32_t **ijk,
+                        uint64_t **bin, uint8_t **acc)
+{
+    int64_t n = 0;
+    for (int64_t u = 0; u < n_units; ++u)
+        n += bufs[u].n;
+    *n_out = n;
+    *ijk = malloc((size_t)(n ? n : 1) * 3 * sizeof(int32_t));
+    *bin = malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
+    if (acc)
+        *acc = malloc((size_t)(n ? n : 1));
+    int64_t p = 0;
+    for (int64_t u = 0; u < n_units; ++u) {
+        blk_buf *b = bufs + u;
+        if (b->n) {
+            memcpy(*ijk + 3 * p, b->ijk, (size_t)b->n * 3 * sizeof(int32_t));
+            memcpy(*bin + p, b->bin, (size_t)b->n * sizeof(uint64_t));
+            if (acc)
+                memcpy(*acc + p, b->acc, (size_t)b->n);
+        }
+        p += b->n;
+        free(b->ijk);
+        free(b->bin);
+        free(b->acc);
+    }
+}
+
+int orc_run_blocks(const orc_hit *hits, int64_t n_hits, const int64_t *offsets, int32_t n_events,
+                   const orc_setup *s, int32_t n_threads, const int32_t *count_slot,
+                   const uint8_t *keep_sel, const uint8_t *flip_sel, int32_t *counts,
+                   orc_block_result *res)
+{
+    memset(res, 0, sizeof(*res));
+    if (n_events != 1 || offsets[0] != 0 || offsets[1] != n_hits)
+        return -1;
+    for (int64_t h = 0; h < n_hits; ++h)
+        if (hits[h].layer < 0 || hits[h].layer >= s->n_layers)
+            return -1;
+    const int L = s->n_layers;
+    const uint64_t inner = (uint64_t)s->n[2] * s->n[3] * s->n[4];
+    /* the layer lists, in input order */
+    int64_t *lo = calloc((size_t)L + 1, sizeof(int64_t));
+    int32_t *lay_idx = malloc((size_t)(n_hits > 0 ? n_hits : 1) * sizeof(int32_t));
+    for (int64_t h = 0; h < n_hits; ++h)
+        lo[hits[h].layer + 1]++;
+    for (int l = 0; l < L; ++l)
+        lo[l + 1] += lo[l];
+    {
+        int64_t *fill = malloc((size_t)L * sizeof(int64_t));
+        for (int l = 0; l < L; ++l)
+            fill[l] = lo[l];
+        for (int64_t h = 0; h < n_hits; ++h)
+            lay_idx[fill[hits[h].layer]++] = (int32_t)h;
+        free(fill);
+    }
+    /* work units: (triple, inner hit) */
+    int64_t n_units = 0;
+    for (int t = 0; t < s->n_triples; ++t) {
+        const int a = s->triples[3 * t], b = s->triples[3 * t + 1], c = s->triples[3 * t + 2];
+        n_units += lo[a + 1] - lo[a];
+        res->n_triplets += (lo[a + 1] - lo[a]) * (lo[b + 1] - lo[b]) * (lo[c + 1] - lo[c]);
+    }
+    int32_t *u_triple = malloc((size_t)(n_units ? n_units : 1) * sizeof(int32_t));
+    int64_t *u_i = malloc((size_t)(n_units ? n_units : 1) * sizeof(int64_t));
+    {
+        int64_t u = 0;
+        for (int t = 0; t < s->n_triples; ++t) {
+            const int a = s->triples[3 * t];
+            for (int64_t i = lo[a]; i < lo[a + 1]; ++i) {
+                u_triple[u] = t;
+                u_i[u] = i;
+                ++u;
+            }
+        }
+    }
+    blk_buf *kb = calloc((size_t)(n_units ? n_units : 1), sizeof(blk_buf));
+    blk_buf *fb = calloc((size_t)(n_units ? n_units : 1), sizeof(blk_buf));
+    int64_t n_deg = 0;
+#ifdef _OPENMP
+    if (n_threads > 0)
+        omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : n_deg)
+#endif
+    for (int64_t u = 0; u < n_units; ++u) {
+        const int t = u_triple[u];
+        const int b = s->triples[3 * t + 1], c = s->triples[3 * t + 2];
+        const int32_t hi_ = lay_idx[u_i[u]];
+        const double p1[3] = {hits[hi_].x, hits[hi_].y, hits[hi_].z};
+        for (int64_t jj = lo[b]; jj < lo[b + 1]; ++jj) {
+            const int32_t hj = lay_idx[jj];
+            const double p2[3] = {hits[hj].x, hits[hj].y, hits[hj].z};
+            for (int64_t kk = lo[c]; kk < lo[c + 1]; ++kk) {
+                const int32_t hk = lay_idx[kk];
+                const double p3[3] = {hits[hk].x, hits[hk].y, hits[hk].z};
+                double par[5];
+                int anti;
+                if (orc_fit_flags(p1, p2, p3, s->b_tesla, s->eps_rel, par, &anti) != ORC_OK) {
+                    n_deg++;
+                    continue;
+                }
+                uint64_t bin;
+                int amb, near;
+                const int acc = orc_bin(s, par, &bin, &amb, &near);
+                if (acc) {
+                    const uint64_t blk = bin / inner;
+                    const int32_t slot = count_slot[blk];
+                    if (slot >= 0) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                        counts[(uint64_t)slot * inner + bin % inner]++;
+                    }
+                    if (keep_sel[blk])
+                        blk_push(kb + u, hi_, hj, hk, bin, 1);
+                    if ((amb || anti) && (flip_sel[blk] || anti))
+                        blk_push(fb + u, hi_, hj, hk, bin, 1);
+                } else if (near || anti) {
+                    blk_push(fb + u, hi_, hj, hk, 0, 0);
+                }
+            }
+        }
+    }
+    res->n_degenerate = n_deg;
+    blk_flatten(kb, n_units, &res->n_keep, &res->keep_ijk, &res->keep_bin, NULL);
+    blk_flatten(fb, n_units, &res->n_flip, &res->flip_ijk, &res->flip_bin, &res->flip_acc);
+    free(kb);
+    free(fb);
+    free(u_triple);
+    free(u_i);
+    free(lo);
+    free(lay_idx);
+    return 0;
+}
+
+void orc_block_result_free(orc_block_result *res)
+{
+    free(res->keep_ijk);
+    free(res->keep_bin);
+    free(res->flip_ijk);
+    free(res->flip_bin);
+    free(res->flip_acc);
+    memset(res, 0, sizeof(*res));
+}
+
+/* The peak rule (Sec. 7 and Fig. 3: candidates are local maxima of the parameter space,
+ * with the stated threshold and tie-break) for every bin of the keep blocks, from block
+ * counts laid out as orc_run_blocks writes them.  Every neighbour block of a keep block must
+ * be counted.  Writes candidates in increasing bin order; returns their number, or -1 if a
+ * needed neighbour block is not counted, or -2 if cap is too small. */
+int64_t orc_block_peaks(const orc_setup *s, const int32_t *count_slot, const int32_t *counts,
+                        const uint8_t *keep_sel, int32_t threshold, uint64_t *out_bin,
+                        int32_t *out_votes, int64_t cap)
+{
+    const int n0 = s->n[0], n1 = s->n[1], n2 = s->n[2], n3 = s->n[3], n4 = s->n[4];
+    const uint64_t inner = (uint64_t)n2 * n3 * n4;
+    int64_t nc = 0;
+    for (int i0 = 0; i0 < n0; ++i0)
+        for (int i1 = 0; i1 < n1; ++i1) {
+            if (!keep_sel[i0 * n1 + i1])
+                continue;
+            const int32_t slot = count_slot[i0 * n1 + i1];
+            if (slot < 0)
+                return -1;
+            for (uint64_t r = 0; r < inner; ++r) {
+                const int32_t h = counts[(uint64_t)slot * inner + r];
+                if (h < threshold)
+                    continue;
+                const int i2 = (int)(r / ((uint64_t)n3 * n4));
+                const int i3 = (int)((r / (uint64_t)n4) % (uint64_t)n3);
+                const int i4 = (int)(r % (uint64_t)n4);
+                const uint64_t bin = ((uint64_t)i0 * n1 + (uint64_t)i1) * inner + r;
+                int is_peak = 1;
+                for (int d0 = -1; d0 <= 1 && is_peak; ++d0)
+                    for (int d1 = -1; d1 <= 1 && is_peak; ++d1)
+                        for (int d2 = -1; d2 <= 1 && is_peak; ++d2)
+                            for (int d3 = -1; d3 <= 1 && is_peak; ++d3)
+                                for (int d4 = -1; d4 <= 1 && is_peak; ++d4) {
+                                    if (!d0 && !d1 && !d2 && !d3 && !d4)
+                                        continue;
+                                    int j0 = i0 + d0;
+                                    const int j1 = i1 + d1, j2 = i2 + d2, j3 = i3 + d3,
+                                              j4 = i4 + d4;
+                                    if (s->periodic & 1)
+                                        j0 = (j0 + n0) % n0;
+                                    else if (j0 < 0 || j0 >= n0)
+                                        continue;
+                                    if (j1 < 0 || j1 >= n1 || j2 < 0 || j2 >= n2 || j3 < 0 ||
+                                        j3 >= n3 || j4 < 0 || j4 >= n4)
+                                        continue;
+                                    const int32_t ns = count_slot[j0 * n1 + j1];
+                                    if (ns < 0)
+                                        return -1;
+                                    const uint64_t nr = ((uint64_t)j2 * n3 + (uint64_t)j3) * n4 + (uint64_t)j4;
+                                    const int32_t hn = counts[(uint64_t)ns * inner + nr];
+                                    const uint64_t nbin = ((uint64_t)j0 * n1 + (uint64_t)j1) * inner + nr;
+                                    if (hn > h || (hn == h && nbin < bin))
+                                        is_peak = 0;
+                                }
+                if (is_peak) {
+                    if (nc >= cap)
+                        return -2;
+                    out_bin[nc] = bin;
+                    out_votes[nc] = h;
+                    ++nc;
+                }
+            }
+        }
+    return nc;
+}
+
 int32_t orc_max_threads(void)
 {
 #ifdef _OPENMP

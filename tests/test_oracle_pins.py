@@ -473,3 +473,94 @@ def test_golden_bin_centres():
             periodic=np.array(b["periodic"]), threshold=1)
         got = oracle.bin_centres(np.array([c["bin"]], dtype=np.int64), setup)[0]
         assert np.allclose(got, c["expected"], rtol=0, atol=1e-12), (c["name"], got, c["expected"])
+
+
+def _blocks_around(setup, centre_blocks):
+    n0, n1 = int(setup.n[0]), int(setup.n[1])
+    out = set()
+    for i0, i1 in centre_blocks:
+        for d0 in (-1, 0, 1):
+            for d1 in (-1, 0, 1):
+                j1 = i1 + d1
+                if 0 <= j1 < n1:
+                    out.add(((i0 + d0) % n0, j1))
+    return sorted(out)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_block_enumeration_equals_full_enumeration(periodic):
+    # the output-restricted definition must give exactly the full definition's counts,
+    # accepted triplets and candidates inside its blocks (blocks at the phi0 wrap included)
+    cfg = ev.load_workload("barrel4_20trk")
+    setup = oracle.OracleSetup.from_workload(cfg)
+    setup.periodic = np.array([periodic] + [False] * 4)
+    b = ev.concat([ev.make_batch(cfg, seed=61), ev.make_batch(cfg, seed=62)]).event(0)
+    n0, n1 = int(setup.n[0]), int(setup.n[1])
+    inner = int(np.prod(setup.n[2:]))
+    full = oracle.enumerate_batch(b.xyz, b.layer, b.offsets, setup)
+    ub0, cnt0 = np.unique(full["bin"], return_counts=True)
+    cand0, _ = oracle.peaks(ub0, cnt0, setup)
+    # blocks of some candidates, and blocks on both sides of the phi0 wrap
+    keep = sorted({(int(c // inner) // n1, int(c // inner) % n1) for c in cand0[::5]} |
+                  {(0, 8), (n0 - 1, 8), (5, 0), (9, n1 - 1)})
+    count = _blocks_around(setup, keep)
+    if not periodic:
+        # without wrap the neighbour rows are the in-range ones; blocks across the wrap are
+        # absent and must not be needed
+        count = sorted({(i0 + d0, i1 + d1) for i0, i1 in keep for d0 in (-1, 0, 1)
+                        for d1 in (-1, 0, 1) if 0 <= i0 + d0 < n0 and 0 <= i1 + d1 < n1})
+    flip = _blocks_around(setup, count)
+    blk = oracle.enumerate_blocks(b.xyz, b.layer, setup, count, keep, flip)
+    assert blk["n_triplets"] == full["n_triplets"]
+    assert blk["n_degenerate"] == full["n_degenerate"]
+    fb = full["bin"]
+    for q, (i0, i1) in enumerate(count):
+        sel = fb // inner == i0 * n1 + i1
+        dense = np.bincount(fb[sel] % inner, minlength=inner)
+        assert np.array_equal(blk["counts"][q], dense), (i0, i1)
+    kset = np.isin(fb // inner, [i0 * n1 + i1 for i0, i1 in keep])
+    assert np.array_equal(np.sort(parity_keys(blk["keep_ijk"])), np.sort(parity_keys(full["ijk"][kset])))
+    # every edge-ambiguous accepted triplet of a flip block, and every near-accepted one, is
+    # listed
+    fsel = np.isin(fb // inner, [i0 * n1 + i1 for i0, i1 in flip]) & full["amb"]
+    listed = set(parity_keys(blk["flip_ijk"]).tolist())
+    assert set(parity_keys(full["ijk"][fsel]).tolist()) <= listed
+    assert set(parity_keys(full["near_ijk"]).tolist()) <= listed
+    # candidates of the keep blocks: the plain C rule over the block counts equals the
+    # numpy rule over the whole histogram
+    cb, cv = oracle.block_peaks(blk, setup, keep)
+    ub, cnt = np.unique(fb, return_counts=True)
+    rb, rv = oracle.peaks(ub, cnt, setup)
+    rsel = np.isin(rb // inner, [i0 * n1 + i1 for i0, i1 in keep])
+    assert len(rb[rsel]) > 0
+    assert np.array_equal(cb, rb[rsel]) and np.array_equal(cv, rv[rsel])
+
+
+def test_block_peaks_on_random_histograms():
+    # dense random counts: the C block rule against the numpy rule, wrap and edges included
+    rng = np.random.default_rng(7)
+    setup = oracle.OracleSetup(b_tesla=3.8, n_layers=3, triples=np.array([[0, 1, 2]], np.int32),
+                               lo=np.zeros(5), hi=np.ones(5), n=np.array([5, 4, 3, 4, 3]),
+                               periodic=np.array([True, False, False, False, False]),
+                               threshold=3)
+    n0, n1 = 5, 4
+    inner = 3 * 4 * 3
+    for trial in range(20):
+        h = rng.integers(0, 6, size=n0 * n1 * inner)
+        ub = np.nonzero(h)[0]
+        keep = [(int(rng.integers(0, n0)), int(rng.integers(0, n1))) for _ in range(3)]
+        keep = sorted(set(keep))
+        count = _blocks_around(setup, keep)
+        counts = np.stack([h[(i0 * n1 + i1) * inner:(i0 * n1 + i1 + 1) * inner] for i0, i1 in count])
+        slot = -np.ones(n0 * n1, np.int32)
+        for q, (i0, i1) in enumerate(count):
+            slot[i0 * n1 + i1] = q
+        cb, cv = oracle.block_peaks(dict(slot=slot, counts=counts.astype(np.int32)), setup, keep)
+        rb, rv = oracle.peaks(ub.astype(np.int64), h[ub].astype(np.int64), setup)
+        rsel = np.isin(rb // inner, [i0 * n1 + i1 for i0, i1 in keep])
+        assert np.array_equal(cb, rb[rsel]) and np.array_equal(cv, rv[rsel]), trial
+
+
+def parity_keys(ijk):
+    ijk = np.asarray(ijk, dtype=np.int64).reshape(-1, 3)
+    return (ijk[:, 0] << 42) | (ijk[:, 1] << 21) | ijk[:, 2]
