@@ -363,7 +363,7 @@ def main():
                    "tuning": tuning, "candidate_fit": bool(args.with_fit)},
         "hit_triplets_per_s": value * n_trip,
         "stats": {k: stats[k] for k in ("n_triplets", "n_fit", "n_exact", "n_votes", "n_fp64", "n_candidates",
-                                        "n_hit_ids", "n_work_items")},
+                                        "n_hit_ids", "n_work_items", "n_plateau", "n_cand_votes")},
         "roofline": {"bound": "alu", "kernel": "k_vote", "achieved": achieved, "peak": alu_peak,
                      "unit": "TFLOP/s", "frac": (achieved / alu_peak) if achieved else None,
                      "traffic": vote_traffic(args.workload, tuning), "vote_kernel_ms": vote_ms,
@@ -393,7 +393,7 @@ def main():
                       if stage_ms.get("peaks") else None,
                       "peak_gbs": hbm_peak, "peak_source": "measured (MEASURED_PEAKS.json)",
                       "basis": "one read of the event's dense histogram (4 B per bin)"},
-            "assign": {"kernels": "k_assign_fill, k_cand_hits, scans, k_compact",
+            "assign": {"kernels": "k_assign_scan, k_assign_cvotes, k_cand_hits, scans, k_compact",
                        "bytes": 4 * stats["n_votes"], "ms": stage_ms.get("assign"),
                        "achieved_gbs": (4 * stats["n_votes"] / (stage_ms["assign"] / 1000.0) / 1e9)
                        if stage_ms.get("assign") else None,
@@ -422,53 +422,24 @@ def main():
 
 
 def run_variants(args, local):
-    """Batched (one call per memory-sized sub-batch of the 256-event uneven workload),
-    the same events through the plain path one call each, and served (Poisson arrivals
-    through the continuous-batching server).  Device-resident inputs for the first two,
-    host inputs (the server's own copies) for the third."""
+    """Batched (the 256-event uneven workload in one call when its vote lists fit the free
+    device memory, else in the largest memory-sized sub-batches), the same events through
+    the plain path one call each, and serving: the plain host path and the continuous-
+    batching server driven by the same Poisson arrival stream."""
     import torch
     from paper_1305_4855_gb300 import events as ev
-    from paper_1305_4855_gb300.trk import Reconstructor, Server
+    from paper_1305_4855_gb300.trk import Reconstructor
     cfg = ev.load_workload(BATCH_WORKLOAD)
     batch = ev.make_batch(cfg, n_events=args.batch_events)
-    n_trip = int(ev.layer_triplet_count(batch, cfg["geometry"]["triples"]).sum())
+    trip_ev = ev.layer_triplet_count(batch, cfg["geometry"]["triples"]).astype(np.int64)
+    n_trip = int(trip_ev.sum())
     out = {"candidate_fit": run_fit(args, local),
            "hough2d": {w: run_hough2d(w, local) for w in ("sht_toy50", "curved_ip200", "sht_jets")}}
-    # --- batched: sub-batches of SUB events, each one trk_reconstruct (one graph launch)
-    sub = 32
     per_event_max = int(np.diff(batch.offsets).max())
-    rec = Reconstructor(cfg, max_events=sub, max_hits=sub * per_event_max, device=local,
-                        vote_capacity=1 << 32, cand_capacity=1 << 23, assign_capacity=1 << 28,
-                        peak_scratch_bytes=8 << 30)
     packed = torch.from_numpy(batch.packed()).cuda()
-    chunks = []
-    for s0 in range(0, batch.n_events, sub):
-        s1 = min(batch.n_events, s0 + sub)
-        a, b_ = int(batch.offsets[s0]), int(batch.offsets[s1])
-        chunks.append((packed[a:b_].contiguous(),
-                       torch.from_numpy(batch.offsets[s0:s1 + 1] - a).cuda()))
     stream = torch.cuda.Stream()
-    tuning = rec.autotune(chunks[0][0], chunks[0][1], reps=1, stream=stream)
-    with torch.cuda.stream(stream):
-        for h_, o_ in chunks[:1]:
-            rec.reconstruct_device(h_, o_, stream=stream)
-    torch.cuda.synchronize()
-    st_ev, en_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    failed = 0
-    with torch.cuda.stream(stream):
-        st_ev.record(stream)
-        for h_, o_ in chunks:
-            rc = rec.reconstruct_device(h_, o_, stream=stream)
-            failed += int(rc != 0)
-        en_ev.record(stream)
-    torch.cuda.synchronize()
-    ms = st_ev.elapsed_time(en_ev)
-    out["batched"] = {"workload": BATCH_WORKLOAD, "events": batch.n_events, "sub_batch": sub,
-                      "events_per_s": batch.n_events / (ms / 1000.0),
-                      "hit_triplets_per_s": n_trip / (ms / 1000.0), "ms": ms,
-                      "calls_with_capacity_errors": failed, "tuning": tuning}
-    rec.close()
-    # --- the same events through the plain path, one call per event
+    # --- the same events through the plain path, one call per event (also measures the
+    #     acceptance fraction that sizes the batched call's vote list)
     rec = Reconstructor(cfg, max_events=1, max_hits=per_event_max, device=local,
                         vote_capacity=1 << 29, cand_capacity=1 << 21, assign_capacity=1 << 25)
     evs = [(packed[int(batch.offsets[e]):int(batch.offsets[e + 1])].contiguous(),
@@ -478,24 +449,164 @@ def run_variants(args, local):
     with torch.cuda.stream(stream):
         rec.reconstruct_device(evs[0][0], evs[0][1], stream=stream)
     torch.cuda.synchronize()
-    lat = []
+    lat, done_t, votes = [], [], 0
+    plain_stages = {}
+
+    def add_stages(acc, st):
+        for k, v in st.items():
+            acc[k] = acc.get(k, 0.0) + v
+    t0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        st_ev.record(stream)
         for h_, o_ in evs:
-            t0 = time.perf_counter()
-            rec.reconstruct_device(h_, o_, stream=stream)
-            lat.append(time.perf_counter() - t0)
-        en_ev.record(stream)
-    torch.cuda.synchronize()
-    ms = st_ev.elapsed_time(en_ev)
-    out["plain_on_batch_events"] = {"events_per_s": batch.n_events / (ms / 1000.0),
-                                    "hit_triplets_per_s": n_trip / (ms / 1000.0), "ms": ms,
-                                    "p50_ms": 1000 * float(np.percentile(lat, 50)),
-                                    "p99_ms": 1000 * float(np.percentile(lat, 99))}
+            t1 = time.perf_counter()
+            rec.reconstruct_device(h_, o_, stream=stream)    # returns after its counts sync
+            t2 = time.perf_counter()
+            lat.append(t2 - t1)
+            done_t.append(t2 - t0)
+            votes += rec.stats()["n_votes"]
+            add_stages(plain_stages, rec.stage_ms(stream))   # events of the call (no sync left)
+    wall = time.perf_counter() - t0
+    out["plain_on_batch_events"] = {
+        "events_per_s": batch.n_events / wall, "hit_triplets_per_s": n_trip / wall, "ms": 1000 * wall,
+        "p50_ms": 1000 * float(np.percentile(lat, 50)), "p99_ms": 1000 * float(np.percentile(lat, 99)),
+        "all_at_once": {"p50_ms": 1000 * float(np.percentile(done_t, 50)),
+                        "p99_ms": 1000 * float(np.percentile(done_t, 99))},
+        "votes": int(votes), "acceptance": votes / n_trip,
+        "device_stage_ms": plain_stages}
     rec.close()
-    # --- served: open-loop Poisson arrivals (a prefix of the 1e6-event stream)
-    out["served"] = run_served(args, cfg, batch, out["batched"]["events_per_s"], local)
+    # --- batched: the whole mix in one call if its vote list and histograms fit
+    free_b = torch.cuda.mem_get_info()[0]
+    nbins = int(np.prod(cfg["binning"]["n"]))
+    accept = 1.1 * votes / n_trip                          # 10 % headroom on the measured rate
+
+    def call_bytes(first, last):
+        v = accept * trip_ev[first:last].sum()
+        e = last - first
+        return 8.75 * v + e * (4 * nbins + 8 * ((nbins + 31) // 32)) + (3 << 30)
+    sub = batch.n_events
+    while sub > 1 and max(call_bytes(s0, min(batch.n_events, s0 + sub))
+                          for s0 in range(0, batch.n_events, sub)) > 0.9 * free_b:
+        sub //= 2
+    vcap = int(max(accept * trip_ev[s0:s0 + sub].sum() for s0 in range(0, batch.n_events, sub)))
+    rec = Reconstructor(cfg, max_events=sub, max_hits=int(batch.offsets[-1]), device=local,
+                        vote_capacity=vcap, cand_capacity=1 << 25, assign_capacity=1 << 29)
+    chunks = []
+    for s0 in range(0, batch.n_events, sub):
+        s1 = min(batch.n_events, s0 + sub)
+        a, b_ = int(batch.offsets[s0]), int(batch.offsets[s1])
+        chunks.append((packed[a:b_].contiguous(),
+                       torch.from_numpy(batch.offsets[s0:s1 + 1] - a).cuda(), s1 - s0))
+    tune_n = min(32, sub)
+    a_, b_ = int(batch.offsets[0]), int(batch.offsets[tune_n])
+    tuning = rec.autotune(packed[a_:b_].contiguous(),
+                          torch.from_numpy(batch.offsets[:tune_n + 1] - a_).cuda(), reps=1,
+                          stream=stream)
+    with torch.cuda.stream(stream):
+        rec.reconstruct_device(chunks[0][0], chunks[0][1], stream=stream)    # graph capture
+    torch.cuda.synchronize()
+    failed, done_b, batch_stages = 0, [], {}
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for h_, o_, n_ in chunks:
+            rc = rec.reconstruct_device(h_, o_, stream=stream)
+            failed += int(rc != 0)
+            done_b += [time.perf_counter() - t0] * n_
+            add_stages(batch_stages, rec.stage_ms(stream))
+    wall = time.perf_counter() - t0
+    out["batched"] = {"workload": BATCH_WORKLOAD, "events": batch.n_events, "sub_batch": sub,
+                      "calls": len(chunks), "events_per_s": batch.n_events / wall,
+                      "hit_triplets_per_s": n_trip / wall, "ms": 1000 * wall,
+                      "all_at_once": {"p50_ms": 1000 * float(np.percentile(done_b, 50)),
+                                      "p99_ms": 1000 * float(np.percentile(done_b, 99))},
+                      "calls_with_capacity_errors": failed, "tuning": tuning,
+                      "device_stage_ms": batch_stages,
+                      "memory": {"free_gb": free_b / 1e9, "vote_capacity": vcap,
+                                 "largest_call_gb": max(call_bytes(s0, min(batch.n_events, s0 + sub))
+                                                        for s0 in range(0, batch.n_events, sub)) / 1e9,
+                                 "whole_mix_gb": call_bytes(0, batch.n_events) / 1e9,
+                                 "basis": "8.75 B per vote (bin, code, chunk record) at 1.1 x the "
+                                          "measured acceptance, 4 B per bin and 8 B per 32 bins "
+                                          "per event, 3 GB of other pools"}}
+    rec.close()
+    # --- serving, like for like: host events in, results on the host, same arrivals
+    out["serving"] = run_serving(args, cfg, batch, local)
     return out
+
+
+def run_serving(args, cfg, batch, local):
+    """Plain host path (one trk_reconstruct_host per event, first come first served, on one
+    thread) and the server, each fed the same events at the same Poisson arrival times.
+    Latency: arrival to results on the host.  The rate is a stated fraction of the plain
+    path's measured capacity; a second run offers every event at once (saturation)."""
+    from paper_1305_4855_gb300.trk import Reconstructor, Server
+    per_event_max = int(np.diff(batch.offsets).max())
+    hosts = [np.ascontiguousarray(batch.packed()[int(batch.offsets[e]):int(batch.offsets[e + 1])])
+             for e in range(batch.n_events)]
+    import torch
+    pinned = [torch.from_numpy(h).pin_memory() for h in hosts]
+    offs = [torch.tensor([0, len(h)], dtype=torch.int64).pin_memory() for h in hosts]
+    rec = Reconstructor(cfg, max_events=1, max_hits=per_event_max, device=local,
+                        vote_capacity=1 << 29, cand_capacity=1 << 21, assign_capacity=1 << 25)
+    rec.reconstruct_host(pinned[0], offs[0])
+    # plain capacity: every event back to back through the host path
+    t0 = time.perf_counter()
+    for e in range(len(hosts)):
+        rec.reconstruct_host(pinned[e], offs[e])
+    cap_plain = len(hosts) / (time.perf_counter() - t0)
+    frac = 0.8
+    rate = frac * cap_plain
+    n = min(len(hosts), max(64, int(rate * args.serve_seconds / 2)))
+    rng = np.random.default_rng(5)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+
+    def pct(x):
+        return {"p50_ms": 1000 * float(np.percentile(x, 50)),
+                "p99_ms": 1000 * float(np.percentile(x, 99)),
+                "p999_ms": 1000 * float(np.percentile(x, 99.9))}
+
+    def plain_run(arr):
+        lat = []
+        t0 = time.perf_counter()
+        for e in range(n):
+            now = time.perf_counter() - t0
+            if arr[e] > now:
+                time.sleep(arr[e] - now)
+            rec.reconstruct_host(pinned[e], offs[e])
+            lat.append(time.perf_counter() - t0 - arr[e])
+        wall = time.perf_counter() - t0
+        return dict(events=n, events_per_s=n / wall, **pct(lat))
+    res = {"arrival_rate_hz": rate, "load": "%.1f of the plain path's measured capacity" % frac,
+           "plain_capacity_events_per_s": cap_plain, "events": n,
+           "plain": plain_run(arrivals), "plain_saturated": plain_run(np.zeros(n))}
+    rec.close()
+
+    def served_run(arr, lanes, lane_events):
+        srv = Server(cfg, lane_events=lane_events, lane_hits=lane_events * per_event_max,
+                     n_lanes=lanes, device=local, vote_capacity=0, cand_capacity=1 << 22,
+                     assign_capacity=1 << 26)
+        for t in [srv.submit(hosts[i]) for i in range(2 * lanes)]:
+            srv.wait(t, 120.0)
+        tickets = []
+        t0 = time.perf_counter()
+        for e in range(n):
+            now = time.perf_counter() - t0
+            if arr[e] > now:
+                time.sleep(arr[e] - now)
+            tickets.append(srv.submit(hosts[e]))
+        lats, nb = [], []
+        for t in tickets:
+            info = srv.wait(t, 600.0)
+            lats.append(info["latency_s"])
+            nb.append(info["batch_events"])
+        wall = time.perf_counter() - t0
+        srv.close()
+        return dict(events=n, events_per_s=n / wall, mean_batch_events=float(np.mean(nb)),
+                    lanes=lanes, lane_events=lane_events, **pct(lats))
+    res["served"] = served_run(arrivals, 2, 4)
+    res["served_saturated"] = served_run(np.zeros(n), 2, 4)
+    res["note"] = ("prefix of the 1e6-event stream: %d events of the batch mix; server lanes "
+                   "sized from free device memory, graphs captured at creation" % n)
+    return res
 
 
 def run_fit(args, local):
@@ -566,61 +677,10 @@ def run_hough2d(workload, local, reps=5):
     return out
 
 
-def run_served(args, cfg, batch, capacity, local):
-    from paper_1305_4855_gb300.trk import Server
-    per_event_max = int(np.diff(batch.offsets).max())
-    hosts = [batch.packed()[int(batch.offsets[e]):int(batch.offsets[e + 1])]
-             for e in range(batch.n_events)]
-    res = {}
-    rates = {"at_0.8_capacity": 0.8 * capacity,
-             "offered_100kHz": float(cfg.get("serving", {}).get("arrival_rate_hz", 100000.0))}
-    serving_cfg = dict(cfg)
-    for name, rate in rates.items():
-        # lanes launch eagerly (the server ignores use_graph): batch sizes vary, and a
-        # first-use graph capture per size would land in the latency tail
-        srv = Server(serving_cfg, lane_events=4, lane_hits=4 * per_event_max, n_lanes=4,
-                     use_graph=0,
-                     device=local, vote_capacity=1 << 31, cand_capacity=1 << 21,
-                     assign_capacity=1 << 26)
-        # warm every lane outside the measurement
-        for t in [srv.submit(hosts[i]) for i in range(8)]:
-            srv.wait(t, 120.0)
-        rng = np.random.default_rng(5)
-        duration = args.serve_seconds / 2
-        # the same number of events in both runs (what 80 % of capacity delivers in
-        # `duration`); at the offered 100 kHz they arrive ~1000x faster than they can be
-        # served, so the queue, and with it the latency, grows over the run
-        n_max = int(0.8 * capacity * duration) + 1
-        gaps = rng.exponential(1.0 / rate, n_max)
-        tickets = []
-        t0 = time.perf_counter()
-        t_next = t0
-        for i in range(n_max):
-            t_next += gaps[i]
-            now = time.perf_counter()
-            if t_next > now:
-                time.sleep(t_next - now)
-            tickets.append(srv.submit(hosts[i % len(hosts)]))
-        lats, nb = [], []
-        for t in tickets:
-            info = srv.wait(t, 600.0)
-            lats.append(info["latency_s"])
-            nb.append(info["batch_events"])
-        wall = time.perf_counter() - t0
-        res[name] = {"offered_hz": rate, "events": len(tickets), "events_per_s": len(tickets) / wall,
-                     "p50_ms": 1000 * float(np.percentile(lats, 50)),
-                     "p99_ms": 1000 * float(np.percentile(lats, 99)),
-                     "p999_ms": 1000 * float(np.percentile(lats, 99.9)),
-                     "mean_batch_events": float(np.mean(nb)), "lanes": 4,
-                     "note": "prefix of the 1e6-event stream: the first %d events" % len(tickets)}
-        srv.close()
-    return res
-
-
 # kernels of one trk_reconstruct call for a one-event batch: pack, schedule, vote,
-# 2 peak passes + the tie pass, 3 scan kernels x 3 scans, candidate emission, assignment,
-# hit lists, compaction, finalize
-LAUNCHES_PER_CALL = 1 + 1 + 1 + 3 + 9 + 1 + 1 + 1 + 1 + 1
+# 2 peak passes + the tie pass, 3 scan kernels x 3 scans, candidate emission, assignment
+# (vote stream + candidate votes), hit lists, compaction, finalize
+LAUNCHES_PER_CALL = 1 + 1 + 1 + 3 + 9 + 1 + 2 + 1 + 1 + 1
 
 # DRAM traffic of one vote-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # ncu captures of the bench workload, one record per vote-kernel tuning; a record stands

@@ -99,9 +99,10 @@ typedef struct trk_options {
     int64_t vote_capacity;                  /* accepted triplets per call */
     int64_t cand_capacity;                  /* candidates per call */
     int64_t assign_capacity;                /* sum over candidates of 3 x votes per call */
-    int64_t peak_scratch_bytes;             /* scratch for the peak filter (>= 8 B x bins) */
-    int32_t tile_i, tile_j;                 /* pair tile of the vote kernel; tile_i*tile_j
-                                               in {64, 128, 256} */
+    int64_t peak_scratch_bytes;             /* scratch of the peak filter (4 B x bins per
+                                               event of a pass) */
+    int32_t tile_i, tile_j;                 /* pair tile of the vote kernel (one block):
+                                               16x16, 8x16, 16x8, 8x8 or 4x16 */
     int32_t k_chunk;                        /* outer-layer hits staged per shared chunk */
     int32_t blocks_per_sm;                  /* persistent vote blocks per SM (0: auto) */
     int32_t use_graph;                      /* capture each call shape in a CUDA graph (the
@@ -181,14 +182,18 @@ typedef struct trk_candidates {
 /* Counters of the last call. */
 typedef struct trk_stats {
     int64_t n_triplets;                     /* sum over events and triples of |La||Lb||Lc| */
-    int64_t n_fit;                          /* triplets through the transverse FP32 fit */
-    int64_t n_exact;                        /* triplets through the exact longitudinal fit */
+    int64_t n_fit;                          /* triplets through the pre-test (survivors of
+                                               the curvature prefilter) */
+    int64_t n_exact;                        /* triplets through the exact FP32 fit */
     int64_t n_votes;                        /* accepted triplets */
     int64_t n_fp64;                         /* fits redone in FP64 */
     int64_t n_candidates;
     int64_t n_hit_ids;
     int64_t n_work_items;
     double ms_total;                        /* device time of the call (events on the stream) */
+    int64_t n_plateau;                      /* bins at their box maximum that share it with a
+                                               neighbour (checked by the tie pass) */
+    int64_t n_cand_votes;                   /* votes in candidate bins */
 } trk_stats;
 
 typedef struct trk_ctx trk_ctx;
@@ -267,7 +272,9 @@ int trk_get_votes(trk_ctx *h, int32_t *dst, uint32_t *bins, int64_t cap, int64_t
  * ijk[3t..3t+2] are indices into hits[0 .. n_hits) (DEVICE).  Writes params[5t..5t+4]
  * (FP32, NaN when degenerate), bins[t] (valid when accepted) and flags[t]: bit 0
  * accepted, bit 1 computed in FP64, bit 2 degenerate, bit 3 index out of range (nothing
- * else written for that triplet).  All DEVICE buffers.  Asynchronous. */
+ * else written for that triplet), bit 4 dropped by the vote kernel's conservative pre-test
+ * (never set for a triplet the exact fit accepts: the vote kernel would lose its vote).
+ * All DEVICE buffers.  Asynchronous. */
 int trk_fit_triplets(trk_ctx *h, const trk_hit *hits, int64_t n_hits, const int32_t *ijk,
                      int64_t n, float *params, uint32_t *bins, int32_t *flags, void *stream);
 
@@ -283,10 +290,14 @@ int trk_profile_stages(trk_ctx *h, float ms[8], void *stream);
  * transfer with the current one's processing (Sec. 8).  A server keeps n_lanes complete
  * handles resident (each with its own pools, stream and graphs, created with
  * lane_options) and a host queue of submitted events.  Each lane runs on its own host
- * thread: when free, it admits every waiting event that fits its capacities
- * (lane_options.max_events events, lane_options.max_hits hits), reconstructs them in one
- * call and files each event's candidates; lanes overlap on the GPU.  An event's results
- * are identical whether it is reconstructed alone, in a batch or by the server. */
+ * thread.  The lanes take the GPU in turn: the lane that gets it admits waiting events,
+ * in arrival order, while they fit its capacities (lane_options.max_events events,
+ * max_hits hits, and the device memory of its vote list) and the backlog (one event more
+ * than the first per 24 waiting: batching delays every event of a batch to its end and
+ * pays only when many wait), reconstructs them in one call, and hands the GPU on as
+ * soon as the kernels are done; it then copies the candidates back and files each event's
+ * results while the next batch computes.  An event's results are identical whether it is
+ * reconstructed alone, in a batch or by the server. */
 typedef struct trk_server trk_server;
 
 typedef struct trk_served_event {
@@ -301,11 +312,15 @@ typedef struct trk_served_event {
 /* Paper Sec. 8 for every call below: the filter unit processes a stream of events, and
  * the next event's transfer and processing overlap the current one's.
  * Create a server of n_lanes (1..16) lanes; each lane allocates one trk handle with
- * lane_options.  fit_candidates is ignored (served events return candidates and hits), and
- * so is use_graph: lanes launch their kernels directly.  A lane runs in its own thread, and
- * while a stream of the process is capturing a CUDA graph, device-wide synchronisation
- * anywhere in the process (handle creation or destruction in another thread, for one) is
- * invalid. */
+ * lane_options: a batch holds at most lane_options.max_events events and max_hits hits.
+ * fit_candidates is ignored (served events return candidates and hits).  With use_graph,
+ * the graph of every batch size is captured here, in the calling thread, so that lanes
+ * only launch graphs.  Device memory decides admission: an event's votes are bounded by
+ * its hit triplets times the largest acceptance fraction seen so far (starting from 1/2),
+ * and a lane admits waiting events, in arrival order, while their bounds fit its vote list
+ * (a batch that overflows anyway is run again one event at a time).  With
+ * lane_options.vote_capacity 0 the vote lists are sized from the device memory free at
+ * creation (cudaMemGetInfo), 90 % of it shared by the lanes. */
 int trk_server_create(trk_server **out, const trk_geometry *geometry, const trk_binning *binning,
                       const trk_options *lane_options, int32_t n_lanes);
 

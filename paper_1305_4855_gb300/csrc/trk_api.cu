@@ -28,9 +28,9 @@ cudaError_t launch_schedule(const CallArgs *args, const DevGeo *geo, const int32
                             Counters *ctr, cudaStream_t s);
 size_t peak_pass1_smem(const FitConst &C, int td);
 cudaError_t launch_peaks(const int32_t *hist, int32_t *m3, const FitConst &C, int g0, int G,
-                         int td, int threshold, const int32_t *status,
-                         unsigned long long *ties, unsigned long long *n_ties, int64_t tie_cap,
-                         int n_sm, cudaStream_t s, bool vec_ok);
+                         int td, int threshold, const int32_t *status, uint32_t *cbits, int64_t W,
+                         uint32_t *filter, unsigned long long *ties, unsigned long long *n_ties,
+                         int64_t tie_cap, int n_sm, cudaStream_t s, bool vec_ok);
 cudaError_t launch_peak_ties(const int32_t *hist, const FitConst &C,
                              const unsigned long long *ties, const unsigned long long *n_ties,
                              int64_t tie_cap, uint32_t *cbits, int64_t W, uint32_t *filter,
@@ -595,9 +595,10 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     for (int g0 = 0; g0 < n_events; g0 += h->group) {
         const int G = (n_events - g0) < h->group ? (n_events - g0) : h->group;
         TRK_CUDA(h, launch_peaks(h->d_hist, h->d_m3, h->C, g0, G, h->td, h->bin.threshold,
-                                 h->d_status, h->d_ties, &ctr->n_ties, h->tie_cap, h->n_sm, s,
-                                 true));
+                                 h->d_status, h->d_cbits, h->W, h->d_filter, h->d_ties,
+                                 &ctr->n_ties, h->tie_cap, h->n_sm, s, true));
     }
+    // the plateau maxima the passes listed
     TRK_CUDA(h, launch_peak_ties(h->d_hist, h->C, h->d_ties, &ctr->n_ties, h->tie_cap, h->d_cbits,
                                  h->W, h->d_filter, &ctr->overflow, h->n_sm, s));
     TRK_CUDA(h, mark(h->ev_st[2]));
@@ -629,6 +630,11 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     aa.fill = h->d_fill;
     aa.assign = h->d_assign;
     aa.assign_cap = o.assign_capacity;
+    // the queue of candidate-vote slots borrows the hit-id buffer, written only later by the
+    // compaction (a candidate vote fills three assignment entries, so the queue needs at most
+    // assign_capacity / 3 slots of the assign_capacity / 2 that fit)
+    aa.cqueue = reinterpret_cast<unsigned long long *>(h->d_hit_ids);
+    aa.cqueue_cap = o.assign_capacity / 2;
     aa.cand_cap = o.cand_capacity;
     aa.ctr = ctr;
     aa.ti = o.tile_i;
@@ -658,33 +664,71 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     return TRK_OK;
 }
 
+// The captured graph of one call shape (n_events), captured on stream s if not cached.
+// Nothing runs during a capture: the graph reads its inputs through the device copy of
+// CallArgs, so it serves every later call of that shape.
+static int graph_for(trk_ctx *h, int n_events, cudaStream_t s, cudaGraphExec_t *out)
+{
+    auto it = h->graphs.find(n_events);
+    if (it == h->graphs.end()) {
+        cudaGraph_t graph;
+        TRK_CUDA(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue(h, n_events, s, true);
+        cudaError_t ec = cudaStreamEndCapture(s, &graph);
+        if (rc != TRK_OK) {
+            if (ec == cudaSuccess)
+                cudaGraphDestroy(graph);
+            return rc;
+        }
+        TRK_CUDA(h, ec);
+        cudaGraphExec_t exec;
+        cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        TRK_CUDA(h, ei);
+        it = h->graphs.emplace(n_events, exec).first;
+    }
+    *out = it->second;
+    return TRK_OK;
+}
+
 static int run_call(trk_ctx *h, int n_events, cudaStream_t s)
 {
     TRK_CUDA(h, cudaMemcpyAsync(h->d_args, h->h_args, sizeof(CallArgs), cudaMemcpyHostToDevice, s));
     if (h->opt.use_graph) {
-        auto it = h->graphs.find(n_events);
-        if (it == h->graphs.end()) {
-            cudaGraph_t graph;
-            TRK_CUDA(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            const int rc = enqueue(h, n_events, s, true);
-            cudaError_t ec = cudaStreamEndCapture(s, &graph);
-            if (rc != TRK_OK) {
-                if (ec == cudaSuccess)
-                    cudaGraphDestroy(graph);
-                return rc;
-            }
-            TRK_CUDA(h, ec);
-            cudaGraphExec_t exec;
-            cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
-            cudaGraphDestroy(graph);
-            TRK_CUDA(h, ei);
-            it = h->graphs.emplace(n_events, exec).first;
-        }
-        TRK_CUDA(h, cudaGraphLaunch(it->second, s));
+        cudaGraphExec_t exec = nullptr;
+        const int rc = graph_for(h, n_events, s, &exec);
+        if (rc != TRK_OK)
+            return rc;
+        TRK_CUDA(h, cudaGraphLaunch(exec, s));
         return TRK_OK;
     }
     return enqueue(h, n_events, s, false);
 }
+
+namespace trk {
+// Captures the graphs of call shapes 1 .. max_events on the handle's own stream, so that
+// later calls only launch them (the server does this before its lane threads start).
+int capture_call_graphs(trk_ctx *h, int max_events)
+{
+    if (!h->opt.use_graph)
+        return TRK_OK;
+    TRK_CUDA(h, cudaSetDevice(h->device));
+    for (int n = 1; n <= max_events && n <= h->opt.max_events; ++n) {
+        cudaGraphExec_t exec = nullptr;
+        const int rc = graph_for(h, n, h->own_stream, &exec);
+        if (rc != TRK_OK)
+            return rc;
+    }
+    return TRK_OK;
+}
+
+// Device bytes one event needs at most for a given vote count: its histogram, candidate
+// bitmap and prefix, and the vote list (bin, code and chunk record per 32 votes).
+int64_t event_device_bytes(const trk_ctx *h, int64_t votes)
+{
+    return 4 * h->nbins + 8 * h->W + votes * 8 + (votes / 32 + 1) * 24;
+}
+}  // namespace trk
 
 static int finish_call(trk_ctx *h, int n_events, trk_candidates *out, cudaStream_t s)
 {
@@ -704,6 +748,8 @@ static int finish_call(trk_ctx *h, int n_events, trk_candidates *out, cudaStream
     st.n_hit_ids = over ? 0 : (int64_t)c.n_hit_ids;
     st.n_work_items = (int64_t)c.n_items;
     st.ms_total = ms;
+    st.n_plateau = (int64_t)c.n_ties;
+    st.n_cand_votes = (int64_t)c.n_cvotes;
     h->last_n_events = n_events;
     int any = 0;
     for (int e = 0; e < n_events; ++e)

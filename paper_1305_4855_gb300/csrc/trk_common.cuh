@@ -69,7 +69,9 @@ struct Counters {
     unsigned long long overflow;     // bit 0 candidate capacity, bit 1 assignment capacity
     unsigned long long n_exact;      // triplets through the exact longitudinal fit
     unsigned long long n_ties;       // bins whose count reaches their box maximum
-    unsigned long long pad[3];
+    unsigned long long pad[1];
+    unsigned long long n_cvotes;     // votes in candidate bins (assignment queue length)
+    unsigned long long pad2[1];
 };
 
 // A run of consecutive votes of one work item in the vote list.
@@ -120,11 +122,18 @@ struct VoteArgs {
 constexpr uint32_t kFilterBits = 192u * 1024u * 8u;
 constexpr uint32_t kFilterWords = kFilterBits / 32u;
 
-__device__ __forceinline__ uint32_t cand_filter_bit(int event, uint32_t bin)
+constexpr uint32_t kFilterEventMul = 0x9E3779B9u;
+
+// The filter bit of (event, bin), with eh = event * kFilterEventMul.
+__device__ __forceinline__ uint32_t cand_filter_bit_h(uint32_t eh, uint32_t bin)
 {
     // multiplicative (Fibonacci) hashing of the key; the high product bits pick the bit
-    const uint32_t key = bin ^ ((uint32_t)event * 0x9E3779B9u);
-    return __umulhi(key * 2654435761u, kFilterBits);
+    return __umulhi((bin ^ eh) * 2654435761u, kFilterBits);
+}
+
+__device__ __forceinline__ uint32_t cand_filter_bit(int event, uint32_t bin)
+{
+    return cand_filter_bit_h((uint32_t)event * kFilterEventMul, bin);
 }
 
 struct AssignArgs {
@@ -149,6 +158,8 @@ struct AssignArgs {
     int32_t *fill;
     int32_t *assign;
     int64_t assign_cap;
+    unsigned long long *cqueue;  // vote slots of the candidate votes (assignment queue)
+    int64_t cqueue_cap;
     int64_t cand_cap;
     Counters *ctr;
     int ti, tj;
@@ -213,8 +224,6 @@ __device__ __forceinline__ float2 vsel(M2 m, float2 a, float2 b)
 template <class V> __device__ __forceinline__ V bc(float a);
 template <> __device__ __forceinline__ float bc<float>(float a) { return a; }
 template <> __device__ __forceinline__ float2 bc<float2>(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float vasin(float a) { return asinf(a); }
-__device__ __forceinline__ float2 vasin(float2 a) { return make_float2(asinf(a.x), asinf(a.y)); }
 
 // det2 (below) over V: a*d - b*c by Kahan's FMA determinant, per half for float2.
 template <class V>
@@ -257,20 +266,85 @@ __device__ __forceinline__ bool in_range_f32(const FitConst &C, int k, float p)
     return p >= C.lo[k] && p < C.hi[k];
 }
 
-// Square root and reciprocal through the MUFU approximations: rsqrtf and the reciprocal
-// of __fdividef are within 2 ulp, so each result is within about 3e-7 relative, 30 times
-// inside the 1e-5 parameter tolerance.  Both the fit and the conservative bounds use them
-// (the bounds' margins are 1e-4); correctly rounded square roots and divisions would cost
-// several times the instructions in a kernel bound by instruction issue.
+// Square root and reciprocal through the special-function unit: the PTX instructions
+// rsqrt.approx.ftz.f32 and rcp.approx.ftz.f32, one MUFU operation each, with subnormal
+// inputs and results flushed to zero (no fix-up instructions around them).  Their errors
+// are within 2 ulp, so each result is within about 3e-7 relative, 30 times inside the
+// 1e-5 parameter tolerance.  Both the fit and the conservative bounds use them (the
+// bounds' margins are 1e-4); correctly rounded square roots and divisions would cost
+// several times the instructions in a kernel bound by instruction issue.  Subnormal
+// magnitudes (below 1.2e-38) do not occur here: lengths are in mm, and every quantity
+// that can vanish (D, |c|) is tested before it is inverted.
+__device__ __forceinline__ float mufu_rsqrt(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float mufu_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float approx_sqrt(float x)
 {
-    return x * rsqrtf(fmaxf(x, 1e-30f));
+    return x * mufu_rsqrt(fmaxf(x, 1e-30f));
 }
-__device__ __forceinline__ float approx_rcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ float approx_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float approx_rcp(float x) { return mufu_rcp(x); }
+__device__ __forceinline__ float approx_div(float a, float b) { return a * mufu_rcp(b); }
 __device__ __forceinline__ float2 approx_sqrt(float2 x)
 {
-    return vmul(x, make_float2(rsqrtf(fmaxf(x.x, 1e-30f)), rsqrtf(fmaxf(x.y, 1e-30f))));
+    return vmul(x, make_float2(mufu_rsqrt(fmaxf(x.x, 1e-30f)), mufu_rsqrt(fmaxf(x.y, 1e-30f))));
+}
+
+// asin(x) for 0 <= x <= 0.75 and atan(x) for 0 <= x <= 1, as x + x t (c1 + c2 t + ...),
+// t = x^2: near-minimax polynomials of the relative error in t, degree 8, fitted by
+// Lawson's algorithm (iteratively reweighted least squares); gen_minimax.py beside this
+// file computes the coefficients and their worst FP32 error (0.89 ulp for the arcsine,
+// 1.47 ulp for the arctangent, Horner with fused multiply-adds).  Nine FMAs and two
+// multiplies, against the general library functions' range reduction and special cases.
+template <class V>
+__device__ __forceinline__ V asin_poly(V x)
+{
+    const V t = vmul(x, x);
+    V r = bc<V>(1.939284503e-01f);
+    r = vfma(r, t, bc<V>(-2.769452333e-01f));
+    r = vfma(r, t, bc<V>(2.225385010e-01f));
+    r = vfma(r, t, bc<V>(-5.583249032e-02f));
+    r = vfma(r, t, bc<V>(4.723963886e-02f));
+    r = vfma(r, t, bc<V>(4.264524207e-02f));
+    r = vfma(r, t, bc<V>(7.511704415e-02f));
+    r = vfma(r, t, bc<V>(1.666640490e-01f));
+    return vfma(vmul(x, t), r, x);
+}
+
+__device__ __forceinline__ float atan_poly(float x)
+{
+    const float t = x * x;
+    float r = 2.849888289e-03f;
+    r = fmaf(r, t, -1.606862433e-02f);
+    r = fmaf(r, t, 4.269151017e-02f);
+    r = fmaf(r, t, -7.504294068e-02f);
+    r = fmaf(r, t, 1.064093336e-01f);
+    r = fmaf(r, t, -1.420364380e-01f);
+    r = fmaf(r, t, 1.999261975e-01f);
+    r = fmaf(r, t, -3.333307207e-01f);
+    return fmaf(x * t, r, x);
+}
+
+// atan2(y, x) in [-pi, pi] from atan_poly of min(|x|, |y|) / max(|x|, |y|) (in [0, 1]) and
+// the octant: pi/2 - a when |y| > |x|, pi - a when x < 0, the sign of y.  (x, y) = (0, 0)
+// gives 0.  pi/2 and pi are added as a float pair (high part + the rounding remainder), so
+// the reflections cost no more than the rounding of their sum.
+__device__ __forceinline__ float atan2_poly(float y, float x)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float a = atan_poly(mn * mufu_rcp(fmaxf(mx, 1e-30f)));
+    float r = ay > ax ? (1.57079637f - a) + -4.37113883e-08f : a;
+    r = x < 0.0f ? (3.14159274f - r) + -8.74227766e-08f : r;
+    return copysignf(r, y);
 }
 
 // Transverse part of the fit: circle, q/pT, d0 and the perigee.
@@ -483,14 +557,17 @@ __device__ __forceinline__ bool z_may_accept(const float4 &p1, const float4 &p2,
 
 // Central angle (0 .. pi) of the arc from P to a hit `chord` away, with `sumlen` the
 // length of (P - c) + (p - c): 2 asin(chord / 2R) up to x = 0.7, and pi - 2 asin(sumlen /
-// 2R) beyond, where the first form is ill-conditioned in FP32.
+// 2R) beyond, where the first form is ill-conditioned in FP32.  Both points lie on the
+// circle, so chord^2 + sumlen^2 = 4R^2: past x = 0.7 the second argument is below 0.715
+// (up to rounding), and both stay inside the [0, 0.75] of asin_poly (the clamp at 0.75
+// never binds for points on the circle).
 template <class V>
 __device__ __forceinline__ V central_angle(V chord, V sumlen, float inv2r)
 {
     const V x = vmul(chord, bc<V>(inv2r));
     const auto far = vnot(vle(x, bc<V>(0.7f)));
-    const V arg = vsel(far, vmin(vmul(sumlen, bc<V>(inv2r)), bc<V>(1.0f)), x);
-    const V h = vmul(bc<V>(2.0f), vasin(arg));
+    const V arg = vsel(far, vmin(vmul(sumlen, bc<V>(inv2r)), bc<V>(0.75f)), x);
+    const V h = vmul(bc<V>(2.0f), asin_poly(arg));
     return vsel(far, vsub(bc<V>(3.14159265f), h), h);
 }
 
@@ -588,7 +665,7 @@ __device__ __forceinline__ int fit_stage_b(const float4 &p1, const float4 &p2, c
 __device__ __forceinline__ bool fit_stage_c(const FitB &r, const FitConst &C, float &phi0,
                                             uint32_t &bin)
 {
-    phi0 = atan2f(-r.sgn * r.cx, r.sgn * r.cy);
+    phi0 = atan2_poly(-r.sgn * r.cx, r.sgn * r.cy);
     uint32_t i0, i1, i2, i3, i4;
     if (!bin_f32(C, 0, phi0, i0) || !bin_f32(C, 1, r.qopt, i1) || !bin_f32(C, 2, r.d0, i2) ||
         !bin_f32(C, 3, r.cot, i3) || !bin_f32(C, 4, r.z0, i4))

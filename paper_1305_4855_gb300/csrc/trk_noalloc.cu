@@ -34,9 +34,9 @@
 namespace trk {
 size_t peak_pass1_smem(const FitConst &C, int td);
 cudaError_t launch_peaks(const int32_t *hist, int32_t *m3, const FitConst &C, int g0, int G,
-                         int td, int threshold, const int32_t *status,
-                         unsigned long long *ties, unsigned long long *n_ties, int64_t tie_cap,
-                         int n_sm, cudaStream_t s, bool vec_ok);
+                         int td, int threshold, const int32_t *status, uint32_t *cbits, int64_t W,
+                         uint32_t *filter, unsigned long long *ties, unsigned long long *n_ties,
+                         int64_t tie_cap, int n_sm, cudaStream_t s, bool vec_ok);
 cudaError_t launch_peak_ties(const int32_t *hist, const FitConst &C,
                              const unsigned long long *ties, const unsigned long long *n_ties,
                              int64_t tie_cap, uint32_t *cbits, int64_t W, uint32_t *filter,
@@ -188,8 +188,9 @@ extern "C" int trk_find_peaks_noalloc(const int32_t *hist, int32_t n_events,
         const bool vec_ok = ((uintptr_t)hg & 15) == 0;
         e = cudaMemsetAsync(d->counters, 0, 2 * sizeof(unsigned long long), s);
         if (e == cudaSuccess)
-            e = launch_peaks(hg, d->scratch, C, 0, G, td, binning->threshold, d->zero, d->ties,
-                             d->counters, TRK_NOALLOC_MAX_BINS, d->n_sm, s, vec_ok);
+            e = launch_peaks(hg, d->scratch, C, 0, G, td, binning->threshold, d->zero,
+                             cand_bits + (size_t)g0 * W, W, nullptr, d->ties, d->counters,
+                             TRK_NOALLOC_MAX_BINS, d->n_sm, s, vec_ok);
         if (e == cudaSuccess)
             e = launch_peak_ties(hg, C, d->ties, d->counters, TRK_NOALLOC_MAX_BINS,
                                  cand_bits + (size_t)g0 * W, W, nullptr, d->counters + 1,

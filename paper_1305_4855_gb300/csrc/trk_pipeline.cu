@@ -195,21 +195,43 @@ __global__ void __launch_bounds__(kSchedThreads) k_schedule(const CallArgs *args
 // 3^5 box, and h[b] > h[m] for the neighbours with a smaller bin number.  The first two
 // conditions say h[b] equals the maximum count over the box, which is separable: pass 1
 // takes it over (d0, cot, z0) in shared memory, pass 2 over (phi0, q/pT) with a sliding
-// window along phi0 and lists the bins that reach it; the tie pass then drops the listed
-// bins that have an equal neighbour with a smaller bin number and sets the candidate bits.
+// window along phi0.
+//
+// Every maximum carries, in bit 0, whether it is attained more than once in its part of the
+// box: key = count << 1, and two keys combine to their maximum, with bit 0 set when their
+// counts are equal (kcomb).  The parts combined at each stage are disjoint, so the final bit
+// says whether the box maximum occurs twice in the 3^5 box.  A bin that reaches the
+// threshold and its box maximum is then a candidate outright when that maximum occurs once
+// (it beats every neighbour), and pass 2 sets its bit; when it occurs again (a plateau) the
+// bin is listed, and the tie pass keeps it unless a neighbour with a smaller bin number has
+// the same count.
 // ---------------------------------------------------------------------------------------
 
-__device__ __forceinline__ int max3i(int a, int b, int c) { return max(max(a, b), c); }
+__device__ __forceinline__ int kcomb(int a, int b)
+{
+    return max(a, b) | (int)((a >> 1) == (b >> 1));
+}
+__device__ __forceinline__ int kcomb3(int a, int b, int c) { return kcomb(kcomb(a, b), c); }
 
-// In-place maximum over {i-1, i, i+1} along a line of n counts with the given stride.
-__device__ __forceinline__ void line_max3(int32_t *p, int n, int stride)
+// In-place combination over {i-1, i, i+1} along a line of n keys with the given stride.
+__device__ __forceinline__ void line_comb3(int32_t *p, int n, int stride)
 {
     int prev = 0, cur = p[0];
     for (int i = 0; i < n; ++i) {
         const int next = (i + 1 < n) ? p[(i + 1) * stride] : 0;
-        p[i * stride] = max3i(prev, cur, next);
+        p[i * stride] = kcomb3(prev, cur, next);
         prev = cur;
         cur = next;
+    }
+}
+
+__device__ __forceinline__ void set_candidate(uint32_t *cbits, int64_t W, uint32_t *filter, int e,
+                                              uint32_t bin)
+{
+    atomicOr(&cbits[(size_t)e * W + (bin >> 5)], 1u << (bin & 31));
+    if (filter) {
+        const uint32_t fb = cand_filter_bit(e, bin);
+        atomicOr(&filter[fb >> 5], 1u << (fb & 31));
     }
 }
 
@@ -279,16 +301,16 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist
         for (int u = 0; u < kL; ++u) {
             const int x = x0 + u * kPeakThreads;
             if (x < total)                   // row-padded: line x / n4, column x % n4
-                sk[x + (int)div_by((uint32_t)x, by4)] = v[u];
+                sk[x + (int)div_by((uint32_t)x, by4)] = v[u] << 1;
         }
     }
     __syncthreads();
     for (int line = tid; line < (rows + 2) * n3; line += kPeakThreads)
-        line_max3(sk + line * P4, n4, 1);
+        line_comb3(sk + line * P4, n4, 1);
     __syncthreads();
     for (int line = tid; line < (rows + 2) * n4; line += kPeakThreads) {
         const int lr = (int)div_by((uint32_t)line, by4), i4 = line - lr * n4;
-        line_max3(sk + lr * n3 * P4 + i4, n3, P4);
+        line_comb3(sk + lr * n3 * P4 + i4, n3, P4);
     }
     __syncthreads();
     int32_t *out = m3 + (size_t)ge * C.nbins + base + (uint32_t)d_start * C.stride[2];
@@ -299,19 +321,22 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist
         int prev = q[0], cur = q[rs];
         for (int r = 0; r < rows; ++r) {
             const int next = q[(r + 2) * rs];
-            out[(size_t)r * plane + line] = max3i(prev, cur, next);
+            out[(size_t)r * plane + line] = kcomb3(prev, cur, next);
             prev = cur;
             cur = next;
         }
     }
 }
 
-// Pass 2: thread per (event, q/pT row, V consecutive inner positions); walks phi0
-// keeping the maxima over q/pT +-1 of the three phi0 rows around the current one.  With
-// V = 4 (inner size a multiple of 4) every load is a 16-byte vector, so a warp reads
-// 512 contiguous bytes per row.  The bins that reach the box maximum are collected per
-// block in shared memory and appended to the global list with one atomic per block tile.
+// Pass 2: thread per (event, q/pT row, V consecutive inner positions, segment of kSeg
+// phi0 rows); walks its segment keeping the maxima over q/pT +-1 of the three phi0 rows
+// around the current one.  Segments (two extra rows of loads per kSeg) give the grid
+// enough threads to fill every SM in even waves.  With V = 4 (inner size a multiple of 4)
+// every load is a 16-byte vector, so a warp reads 512 contiguous bytes per row.  The
+// plateau bins are collected per block in shared memory and appended to the global list
+// with one atomic per block tile.
 constexpr int kTieBuf = 2048;
+constexpr int kSeg = 16;
 
 template <int V>
 struct IntV;
@@ -341,11 +366,11 @@ struct IntV<4> {
 };
 
 template <int V>
-__device__ __forceinline__ IntV<V> vmax(IntV<V> a, const IntV<V> &b)
+__device__ __forceinline__ IntV<V> vcomb(IntV<V> a, const IntV<V> &b)
 {
 #pragma unroll
     for (int c = 0; c < V; ++c)
-        a.v[c] = max(a.v[c], b.v[c]);
+        a.v[c] = kcomb(a.v[c], b.v[c]);
     return a;
 }
 
@@ -353,6 +378,8 @@ template <int V>
 __global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist, const int32_t *m3,
                                                              FitConst C, int g0, int G,
                                                              int threshold, const int32_t *status,
+                                                             uint32_t *cbits, int64_t W,
+                                                             uint32_t *filter,
                                                              unsigned long long *ties,
                                                              unsigned long long *n_ties,
                                                              int64_t tie_cap)
@@ -364,7 +391,8 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist
     const uint32_t inner = C.stride[1];
     const uint32_t innerV = inner / V;
     const bool per0 = (C.periodic & 1) != 0;
-    const int64_t total = (int64_t)G * n1 * innerV;
+    const int nseg = (n0 + kSeg - 1) / kSeg;
+    const int64_t total = (int64_t)G * n1 * innerV * nseg;
     if (threadIdx.x == 0)
         s_n = 0;
     __syncthreads();
@@ -375,7 +403,9 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist
         const uint32_t rest = (uint32_t)(t % innerV) * V;
         const int64_t q = t / innerV;
         const int i1 = (int)(q % n1);
-        const int ge = (int)(q / n1);
+        const int64_t q2 = q / n1;
+        const int seg = (int)(q2 % nseg);
+        const int ge = (int)(q2 / nseg);
         const int e = g0 + ge;
         if (t < total && status[e] == 0) {
             const int32_t *m = m3 + (size_t)ge * C.nbins + rest;
@@ -384,9 +414,9 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist
                 const int32_t *r = m + (size_t)j0 * C.stride[0];
                 IntV<V> x = IntV<V>::load(r + (size_t)i1 * inner);
                 if (i1 > 0)
-                    x = vmax(x, IntV<V>::load(r + (size_t)(i1 - 1) * inner));
+                    x = vcomb(x, IntV<V>::load(r + (size_t)(i1 - 1) * inner));
                 if (i1 + 1 < n1)
-                    x = vmax(x, IntV<V>::load(r + (size_t)(i1 + 1) * inner));
+                    x = vcomb(x, IntV<V>::load(r + (size_t)(i1 + 1) * inner));
                 return x;
             };
             // phi0 rows in groups of kR: the column maxima of rows i0+1 .. i0+kR and the
@@ -396,18 +426,22 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist
 #pragma unroll
             for (int c = 0; c < V; ++c)
                 zero.v[c] = 0;
-            IntV<V> prev = per0 ? colmax(n0 - 1) : zero;
-            IntV<V> cur = colmax(0);
-            const IntV<V> first = cur;
-            for (int c0 = 0; c0 < n0; c0 += kR) {
+            const int r_begin = seg * kSeg;
+            const int r_end = min(n0, r_begin + kSeg);
+            IntV<V> prev = r_begin > 0 ? colmax(r_begin - 1) : (per0 ? colmax(n0 - 1) : zero);
+            IntV<V> cur = colmax(r_begin);
+            for (int c0 = r_begin; c0 < r_end; c0 += kR) {
                 IntV<V> nx[kR], hh[kR];
 #pragma unroll
                 for (int u = 0; u < kR; ++u) {
                     const int r = c0 + u;
                     const int rn = r + 1;
-                    nx[u] = rn < n0 ? colmax(rn) : (rn == n0 && per0 ? first : zero);
-                    hh[u] = r < n0 ? IntV<V>::load(h_e + (size_t)r * C.stride[0] + (size_t)i1 * inner)
-                                   : zero;
+                    // rows past the segment's end are loaded only as the last row's next
+                    nx[u] = rn < n0 ? (r < r_end ? colmax(rn) : zero)
+                                    : (rn == n0 && per0 ? colmax(0) : zero);
+                    hh[u] = r < r_end ? IntV<V>::load(h_e + (size_t)r * C.stride[0] +
+                                                      (size_t)i1 * inner)
+                                      : zero;
                 }
 #pragma unroll
                 for (int u = 0; u < kR; ++u) {
@@ -415,9 +449,14 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist
 #pragma unroll
                     for (int c = 0; c < V; ++c) {
                         const int h = hh[u].v[c];
-                        if (r < n0 && h >= threshold && h == max3i(prev.v[c], cur.v[c], nx[u].v[c])) {
+                        const int box = kcomb3(prev.v[c], cur.v[c], nx[u].v[c]);
+                        if (r < r_end && h >= threshold && h == (box >> 1)) {
                             const uint32_t bin = (uint32_t)r * C.stride[0] + (uint32_t)i1 * inner +
                                                  rest + (uint32_t)c;
+                            if (!(box & 1)) {        // the only maximum of its box
+                                set_candidate(cbits, W, filter, e, bin);
+                                continue;
+                            }
                             const unsigned long long key =
                                 ((unsigned long long)(unsigned)e << 32) | bin;
                             const int k = atomicAdd(&s_n, 1);
@@ -454,6 +493,44 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist
     }
 }
 
+// Warp-cooperative tie test of one bin whose count h reaches its box maximum: true iff a
+// neighbour with a smaller bin number has the same count (that neighbour, or a lower one,
+// keeps the plateau's candidate).  Every lane returns the answer.
+__device__ __forceinline__ bool lower_equal_neighbour(const int32_t *h_e, const FitConst &C,
+                                                      uint32_t bin, int h, int lane)
+{
+    const int n0 = C.n[0];
+    const bool per0 = (C.periodic & 1) != 0;
+    int idx[5];
+    uint32_t rem = bin;
+    for (int k = 0; k < 5; ++k) {
+        idx[k] = (int)(rem / C.stride[k]);
+        rem -= (uint32_t)idx[k] * C.stride[k];
+    }
+    bool beaten = false;
+    for (int o = lane; o < 243; o += 32) {
+        int off = o;
+        uint32_t nb = 0;
+        bool ok = true;
+#pragma unroll
+        for (int k = 4; k >= 0; --k) {
+            const int dk = off % 3 - 1;
+            off /= 3;
+            int j = idx[k] + dk;
+            if (j < 0 || j >= C.n[k]) {
+                if (k == 0 && per0)
+                    j = (j + n0) % n0;
+                else
+                    ok = false;
+            }
+            nb += (uint32_t)j * C.stride[k];
+        }
+        if (ok && nb < bin && h_e[nb] == h)
+            beaten = true;
+    }
+    return __any_sync(kFull, beaten);
+}
+
 // Tie pass: warp per listed bin; candidate unless a neighbour with a smaller bin number
 // has the same count.
 __global__ void k_peak_ties(const int32_t *hist, FitConst C, const unsigned long long *ties,
@@ -469,50 +546,14 @@ __global__ void k_peak_ties(const int32_t *hist, FitConst C, const unsigned long
             atomicOr(overflow, 1ull);
         n = tie_cap;
     }
-    const int n0 = C.n[0];
-    const bool per0 = (C.periodic & 1) != 0;
     for (int64_t i = warp0; i < n; i += nwarps) {
         const unsigned long long key = ties[i];
         const int e = (int)(key >> 32);
         const uint32_t bin = (uint32_t)key;
         const int32_t *h_e = hist + (size_t)e * C.nbins;
-        const int h = h_e[bin];
-        int idx[5];
-        uint32_t rem = bin;
-        for (int k = 0; k < 5; ++k) {
-            idx[k] = (int)(rem / C.stride[k]);
-            rem -= (uint32_t)idx[k] * C.stride[k];
-        }
-        bool beaten = false;
-        for (int o = lane; o < 243; o += 32) {
-            int off = o;
-            uint32_t nb = 0;
-            bool ok = true;
-#pragma unroll
-            for (int k = 4; k >= 0; --k) {
-                const int dk = off % 3 - 1;
-                off /= 3;
-                int j = idx[k] + dk;
-                if (j < 0 || j >= C.n[k]) {
-                    if (k == 0 && per0)
-                        j = (j + n0) % n0;
-                    else
-                        ok = false;
-                }
-                nb += (uint32_t)j * C.stride[k];
-            }
-            const uint32_t nbin = nb;
-            if (ok && nbin < bin && h_e[nbin] == h)
-                beaten = true;
-        }
-        beaten = __any_sync(kFull, beaten);
-        if (!beaten && lane == 0) {
-            atomicOr(&cbits[(size_t)e * W + (bin >> 5)], 1u << (bin & 31));
-            if (filter) {
-                const uint32_t fb = cand_filter_bit(e, bin);
-                atomicOr(&filter[fb >> 5], 1u << (fb & 31));
-            }
-        }
+        const bool beaten = lower_equal_neighbour(h_e, C, bin, h_e[bin], lane);
+        if (!beaten && lane == 0)
+            set_candidate(cbits, W, filter, e, bin);
     }
 }
 
@@ -606,28 +647,32 @@ __device__ __forceinline__ ItemLoc locate_item(int64_t item, const int64_t *item
 
 constexpr int kAssignThreads = 1024;
 
-__global__ void __launch_bounds__(kAssignThreads, 1) k_assign_fill(AssignArgs A)
+// Assignment, part 1: a stream over the bins of the vote list that finds the candidate
+// votes and queues their slots.  Only ~1 % of the votes land in candidate bins, so each
+// thread takes kP groups of four adjacent slots (one 16-byte load each; a warp covers four
+// whole 32-slot chunks) a grid stride apart and issues their bin, chunk count and chunk
+// event loads together; bins are read once, with the streaming (evict-first) hint.  Slots
+// past a chunk's count hold stale data and are discarded.  The shared-memory candidate
+// filter leaves the bitmap lookup to the few votes whose filter bit is set.  A candidate
+// vote's slot goes to the queue with one atomic per warp, so the stream never waits on the
+// dependent loads of the hit decoding (part 2).
+__global__ void __launch_bounds__(kAssignThreads, 1) k_assign_scan(AssignArgs A)
 {
     extern __shared__ uint32_t s_filter[];
     for (uint32_t q = threadIdx.x; q < kFilterWords / 4; q += kAssignThreads)
         reinterpret_cast<uint4 *>(s_filter)[q] = __ldg(reinterpret_cast<const uint4 *>(A.filter) + q);
     __syncthreads();
+    const int lane = threadIdx.x & 31;
     int64_t n_chunks = (int64_t)A.ctr->n_chunks;
     n_chunks = n_chunks < A.chunk_cap ? n_chunks : A.chunk_cap;
     const int64_t n_slots = n_chunks * kWarp;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // Only ~1 % of the votes land in candidate bins, so the kernel is a stream over the
-    // bins of the vote list.  Each thread takes kP groups of four adjacent slots (one
-    // 16-byte load each; a warp covers four whole 32-slot chunks) a grid stride apart and
-    // issues their bin, chunk count and chunk event loads together; bins are read once,
-    // with the streaming (evict-first) hint.  Slots past a chunk's count hold stale data
-    // and are discarded.  The shared-memory candidate filter then leaves the bitmap lookup
-    // (a random 32-byte L2 sector per vote) to the few votes whose filter bit is set, and
-    // only candidate votes read their code.
     constexpr int kP = 4, kU = 4 * kP;
     const int64_t n_quads = n_slots / 4;
-    for (int64_t q0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q0 < n_quads;
-         q0 += kP * stride) {
+    // warp-uniform trip count (the queue append is warp-collective)
+    const int64_t q_warp0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31);
+    for (int64_t qw = q_warp0; qw < n_quads; qw += kP * stride) {
+        const int64_t q0 = qw + lane;
         uint32_t bin[kU];
         int ev[kP];
         int cnt[kP];
@@ -645,48 +690,96 @@ __global__ void __launch_bounds__(kAssignThreads, 1) k_assign_fill(AssignArgs A)
             cnt[u] = in ? __ldg(A.chunk_count + (qd >> 3)) : 0;
             ev[u] = in ? __ldg(A.chunk_event + (qd >> 3)) : 0;
         }
-        // slot within its chunk of vote r of group u: 4 (qd & 7) + r
+        // slot within its chunk of vote r of group u: 4 (qd & 7) + r; the event's part of
+        // the filter hash and its bitmap row are taken once per group
         const int sub = 4 * (int)(q0 & 7);
-        // bitmap word of each vote whose filter bit is set (0 for the others)
-        uint32_t word[kU];
+        uint32_t maybe = 0;           // bit r: vote r is valid and passes the filter
 #pragma unroll
-        for (int r = 0; r < kU; ++r) {
-            const int u = r >> 2;
-            bool look = false;
-            if (sub + (r & 3) < cnt[u]) {
-                const uint32_t fb = cand_filter_bit(ev[u], bin[r]);
-                look = (s_filter[fb >> 5] >> (fb & 31)) & 1u;
-            }
-            word[r] = look ? __ldg(A.cbits + (size_t)ev[u] * A.W + (bin[r] >> 5)) : 0u;
-        }
+        for (int u = 0; u < kP; ++u) {
+            const int nvalid = cnt[u] - sub;
+            const uint32_t eh = (uint32_t)ev[u] * kFilterEventMul;
 #pragma unroll
-        for (int r = 0; r < kU; ++r) {
-            const int u = r >> 2;
-            if (!((word[r] >> (bin[r] & 31)) & 1u))
-                continue;
-            const int e = ev[u];
-            const size_t wpos = (size_t)e * A.W + (bin[r] >> 5);
-            const int64_t c =
-                (int64_t)A.wprefix[wpos] + __popc(word[r] & ((1u << (bin[r] & 31)) - 1u));
-            if (c >= A.cand_cap)
-                continue;
-            const int64_t slot = 4 * (q0 + u * stride) + (r & 3);
-            const int4 loc = __ldg(A.chunk_loc + (slot >> 5));
-            const uint32_t code = __ldg(A.vote_code + slot);
-            const int fslot = atomicAdd(&A.fill[c], 1);
-            const int64_t pos = A.vote_off[c] + 3 * (int64_t)fslot;
-            if (pos + 3 > A.assign_cap) {
-                atomicOr(&A.ctr->overflow, 2ull);
-                continue;
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t fb = cand_filter_bit_h(eh, bin[4 * u + c]);
+                const uint32_t f = (s_filter[fb >> 5] >> (fb & 31)) & 1u;
+                maybe |= (c < nvalid ? f : 0u) << (4 * u + c);
             }
-            const int ip = loc.x + (int)code_i(code);
-            const int jp = loc.y + (int)code_j(code);
-            const int kp = loc.z + (int)code_k(code);
-            const int64_t eb = A.ev_begin[e];
-            A.assign[pos] = __float_as_int(A.packed[ip].w) - (int)eb;
-            A.assign[pos + 1] = __float_as_int(A.packed[jp].w) - (int)eb;
-            A.assign[pos + 2] = __float_as_int(A.packed[kp].w) - (int)eb;
         }
+        uint32_t mine = 0;            // bit r: vote r is a candidate vote
+        if (maybe) {
+            // all lookups issued before any is used, so that they wait together
+            uint32_t word[kU];
+#pragma unroll
+            for (int r = 0; r < kU; ++r)
+                word[r] = ((maybe >> r) & 1u)
+                              ? __ldg(A.cbits + (size_t)ev[r >> 2] * A.W + (bin[r] >> 5))
+                              : 0u;
+#pragma unroll
+            for (int r = 0; r < kU; ++r)
+                mine |= ((word[r] >> (bin[r] & 31)) & 1u) << r;
+        }
+        const int nm = __popc(mine);
+        int incl = nm;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o)
+                incl += v;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        if (total == 0)
+            continue;
+        unsigned long long base = 0;
+        if (lane == 31)
+            base = atomicAdd(&A.ctr->n_cvotes, (unsigned long long)total);
+        base = __shfl_sync(kFull, base, 31);
+        unsigned long long pos = base + (unsigned long long)(incl - nm);
+        while (mine) {
+            const int r = __ffs(mine) - 1;
+            mine &= mine - 1;
+            if ((int64_t)pos < A.cqueue_cap)
+                A.cqueue[pos] = (unsigned long long)(4 * (q0 + (r >> 2) * stride) + (r & 3));
+            ++pos;
+        }
+    }
+}
+
+// Assignment, part 2: thread per queued candidate vote -- its candidate index from the
+// bitmap word prefix, a slot in the candidate's region by an atomic, and the three input
+// hit ids (event-local) decoded from the vote code and its chunk's tile position.
+__global__ void k_assign_cvotes(AssignArgs A)
+{
+    int64_t n = (int64_t)A.ctr->n_cvotes;
+    if (n > A.cqueue_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            atomicOr(&A.ctr->overflow, 2ull);
+        n = A.cqueue_cap;
+    }
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = (int64_t)A.cqueue[q];
+        const int e = __ldg(A.chunk_event + (slot >> 5));
+        const uint32_t bin = __ldg(A.vote_bin + slot);
+        const size_t wpos = (size_t)e * A.W + (bin >> 5);
+        const uint32_t word = __ldg(A.cbits + wpos);
+        const int64_t c = (int64_t)A.wprefix[wpos] + __popc(word & ((1u << (bin & 31)) - 1u));
+        if (c >= A.cand_cap)
+            continue;
+        const int4 loc = __ldg(A.chunk_loc + (slot >> 5));
+        const uint32_t code = __ldg(A.vote_code + slot);
+        const int fslot = atomicAdd(&A.fill[c], 1);
+        const int64_t pos = A.vote_off[c] + 3 * (int64_t)fslot;
+        if (pos + 3 > A.assign_cap) {
+            atomicOr(&A.ctr->overflow, 2ull);
+            continue;
+        }
+        const int ip = loc.x + (int)code_i(code);
+        const int jp = loc.y + (int)code_j(code);
+        const int kp = loc.z + (int)code_k(code);
+        const int eb = (int)A.ev_begin[e];
+        A.assign[pos] = __float_as_int(A.packed[ip].w) - eb;
+        A.assign[pos + 1] = __float_as_int(A.packed[jp].w) - eb;
+        A.assign[pos + 2] = __float_as_int(A.packed[kp].w) - eb;
     }
 }
 
@@ -829,7 +922,7 @@ cudaError_t prepare_pipeline_kernels()
                              200 * 1024);
     if (e != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_assign_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_assign_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(uint32_t) * kFilterWords));
 }
 
@@ -855,30 +948,31 @@ size_t peak_pass1_smem(const FitConst &C, int td)
     return sizeof(int32_t) * (size_t)(td + 2) * C.n[3] * (C.n[4] + 1);
 }
 
-// Peak passes 1 and 2 for events [g0, g0 + G): lists the bins whose count reaches the
-// box maximum (and the threshold).
+// Peak passes 1 and 2 for events [g0, g0 + G): sets the candidate bits of the strict
+// maxima and lists the plateau maxima for the tie pass (cbits must be zeroed).
 // vec_ok: hist is 16-byte aligned, so that pass 2 may read it with 16-byte loads.
 cudaError_t launch_peaks(const int32_t *hist, int32_t *m3, const FitConst &C, int g0, int G,
-                         int td, int threshold, const int32_t *status,
-                         unsigned long long *ties, unsigned long long *n_ties, int64_t tie_cap,
-                         int n_sm, cudaStream_t s, bool vec_ok)
+                         int td, int threshold, const int32_t *status, uint32_t *cbits, int64_t W,
+                         uint32_t *filter, unsigned long long *ties, unsigned long long *n_ties,
+                         int64_t tie_cap, int n_sm, cudaStream_t s, bool vec_ok)
 {
     const size_t sm = peak_pass1_smem(C, td);
     const int nslab = (C.n[2] + td - 1) / td;
     const int64_t grid1 = (int64_t)G * C.n[0] * C.n[1] * nslab;
     k_peak_pass1<<<(unsigned)grid1, kPeakThreads, sm, s>>>(hist, m3, C, g0, td, status);
     const bool vec = vec_ok && (C.stride[1] % 4) == 0;
-    const int64_t threads = (int64_t)G * C.n[1] * C.stride[1] / (vec ? 4 : 1);
+    const int64_t threads = (int64_t)G * C.n[1] * C.stride[1] / (vec ? 4 : 1) *
+                            ((C.n[0] + kSeg - 1) / kSeg);
     int64_t grid2 = (threads + kPeakThreads - 1) / kPeakThreads;
     const int64_t cap2 = (int64_t)n_sm * 32;
     grid2 = grid2 < cap2 ? grid2 : cap2;
     const unsigned g2 = (unsigned)(grid2 > 0 ? grid2 : 1);
     if (vec)
-        k_peak_pass2<4><<<g2, kPeakThreads, 0, s>>>(hist, m3, C, g0, G, threshold, status, ties,
-                                                     n_ties, tie_cap);
+        k_peak_pass2<4><<<g2, kPeakThreads, 0, s>>>(hist, m3, C, g0, G, threshold, status, cbits,
+                                                     W, filter, ties, n_ties, tie_cap);
     else
-        k_peak_pass2<1><<<g2, kPeakThreads, 0, s>>>(hist, m3, C, g0, G, threshold, status, ties,
-                                                     n_ties, tie_cap);
+        k_peak_pass2<1><<<g2, kPeakThreads, 0, s>>>(hist, m3, C, g0, G, threshold, status, cbits,
+                                                     W, filter, ties, n_ties, tie_cap);
     return cudaGetLastError();
 }
 
@@ -921,8 +1015,9 @@ cudaError_t launch_vote_offsets(const trk_candidate *cand, const unsigned long l
 
 cudaError_t launch_assign(const AssignArgs &A, int n_sm, cudaStream_t s)
 {
-    // persistent: one block per SM (the filter takes most of the shared memory)
-    k_assign_fill<<<n_sm, kAssignThreads, sizeof(uint32_t) * kFilterWords, s>>>(A);
+    // the stream: persistent, one block per SM (the filter takes most of the shared memory)
+    k_assign_scan<<<n_sm, kAssignThreads, sizeof(uint32_t) * kFilterWords, s>>>(A);
+    k_assign_cvotes<<<n_sm * 8, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 

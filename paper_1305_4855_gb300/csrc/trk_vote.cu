@@ -38,7 +38,7 @@ __global__ void k_fit_triplets(const trk_hit *hits, int64_t n_hits, const int32_
         FitB r;
         const int st = fit_stage_b(p1, p2, p3, Cw, r);
         if (st == kPass) {
-            float phi0 = atan2f(-r.sgn * r.cx, r.sgn * r.cy);
+            float phi0 = atan2_poly(-r.sgn * r.cx, r.sgn * r.cy);
             par[0] = phi0;
             par[1] = r.qopt;
             par[2] = r.d0;
@@ -62,6 +62,13 @@ __global__ void k_fit_triplets(const trk_hit *hits, int64_t n_hits, const int32_
                 if (r64 == kFit64Accepted)
                     fl |= 1;
             }
+        }
+        // the vote kernel's conservative pre-test (a vote needs it to keep the triplet)
+        {
+            Trans tb;
+            const int sb = fit_transverse_bound(p1, p2, p3, C, tb);
+            if (sb == kReject || (sb == kPass && !z_may_accept(p1, p2, p3, tb, C)))
+                fl |= 16;
         }
         for (int k = 0; k < 5; ++k)
             params[5 * t + k] = par[k];

@@ -123,7 +123,8 @@ class trk_stats(C.Structure):
     _fields_ = [("n_triplets", C.c_int64), ("n_fit", C.c_int64), ("n_exact", C.c_int64),
                 ("n_votes", C.c_int64),
                 ("n_fp64", C.c_int64), ("n_candidates", C.c_int64), ("n_hit_ids", C.c_int64),
-                ("n_work_items", C.c_int64), ("ms_total", C.c_double)]
+                ("n_work_items", C.c_int64), ("ms_total", C.c_double),
+                ("n_plateau", C.c_int64), ("n_cand_votes", C.c_int64)]
 
 
 # numpy view of trk_candidate (48 bytes)

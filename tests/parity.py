@@ -114,3 +114,32 @@ def param_errors(par32: np.ndarray, par64: np.ndarray):
     d = np.abs(par32.astype(np.float64) - par64)
     d[:, 0] = np.abs((par32[:, 0].astype(np.float64) - par64[:, 0] + np.pi) % (2 * np.pi) - np.pi)
     return d
+
+
+def plateau_count(hist: np.ndarray, dims, periodic, threshold: int) -> int:
+    """Bins at or above the threshold that equal the maximum of their 3^5 box while some
+    other bin of the box has the same count: the bins the peak passes hand to the tie pass.
+    Brute force over the 243 offsets (small histograms only); axis k wraps when
+    periodic[k], and a wrapping axis needs at least three bins for the box to hold
+    distinct bins."""
+    h = np.asarray(hist, dtype=np.int64).reshape(dims)
+    p = h
+    for k in range(5):
+        width = [(0, 0)] * 5
+        width[k] = (1, 1)
+        if periodic[k]:
+            assert dims[k] >= 3
+            p = np.pad(p, width, mode="wrap")
+        else:
+            p = np.pad(p, width, mode="constant", constant_values=-1)
+    box = np.full(h.shape, -1, np.int64)
+    views = []
+    for off in itertools.product((0, 1, 2), repeat=5):
+        sl = tuple(slice(o, o + n) for o, n in zip(off, h.shape))
+        v = p[sl]
+        views.append(v)
+        np.maximum(box, v, out=box)
+    eq = np.zeros(h.shape, np.int64)
+    for v in views:
+        eq += (v == box)
+    return int(np.count_nonzero((h >= threshold) & (h == box) & (eq > 1)))

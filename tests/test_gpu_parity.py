@@ -40,8 +40,10 @@ def _run(trk, cfg, batch, max_hits=None, **opts):
     return rec, rec.result(rc), hits
 
 
-def _full_compare(trk, cfg, batch, threads=0, **opts):
-    """Triplets, histograms and candidates of every event of `batch`."""
+def _full_compare(trk, cfg, batch, threads=0, check_plateaus=False, **opts):
+    """Triplets, histograms and candidates of every event of `batch`; with
+    check_plateaus, also the count of plateau bins the peak passes listed."""
+    plateaus = 0
     rec, res, hits = _run(trk, cfg, batch, **opts)
     assert res.rc == 0, rec.error()
     setup = oracle.OracleSetup.from_workload(cfg)
@@ -79,13 +81,19 @@ def _full_compare(trk, cfg, batch, threads=0, **opts):
             assert np.array_equal(cand["params"][gi], oe["cand_params"][oi].astype(np.float32))
         rep.update(n_hist_diff=len(diff), cand=crep["n_compared"])
         reports.append(rep)
+        if check_plateaus:
+            plateaus += parity.plateau_count(gh, dims, setup.periodic, setup.threshold)
+    # the votes in candidate bins, and the plateau bins the tie pass checked
+    assert st["n_cand_votes"] == int(res.cand["votes"].sum())
+    if check_plateaus:
+        assert st["n_plateau"] == plateaus, (st["n_plateau"], plateaus)
     rec.close()
     return reports
 
 
 def test_smoke_barrel4_20trk(trk):
     cfg = ev.load_workload("barrel4_20trk")
-    reps = _full_compare(trk, cfg, ev.make_batch(cfg))
+    reps = _full_compare(trk, cfg, ev.make_batch(cfg), check_plateaus=True)
     assert reps[0]["n_both"] > 1000
 
 
@@ -112,7 +120,7 @@ def test_odd_binnings(trk, dims):
     cfg["events"]["n_tracks"] = 40
     cfg["binning"]["n"] = list(dims)
     cfg["binning"]["threshold"] = 3
-    reps = _full_compare(trk, cfg, ev.make_batch(cfg, seed=23))
+    reps = _full_compare(trk, cfg, ev.make_batch(cfg, seed=23), check_plateaus=True)
     assert reps[0]["n_both"] > 5000
 
 

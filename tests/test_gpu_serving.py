@@ -3,6 +3,8 @@
 Events of the batch workload's multiplicity mix (scaled down so the suite stays quick)
 arrive with random gaps, including bursts; each event's candidates and hit lists from the
 server must equal those of the same event reconstructed alone, whatever batch it shared.
+The server batches by backlog (one more event per 24 waiting), so a burst of 60 events
+makes it run multi-event batches and the gaps after it make it run single events.
 """
 import ctypes
 import time
@@ -46,14 +48,15 @@ def _alone(trk, cfg, e):
 
 
 def test_served_results_equal_alone(trk):
-    cfg, evs = _events(14, seed=91)
+    n_burst = 60
+    cfg, evs = _events(n_burst + 14, seed=91)
     srv = trk.Server(cfg, lane_events=4, lane_hits=8192, n_lanes=2, vote_capacity=1 << 25,
                      cand_capacity=1 << 19, assign_capacity=1 << 23)
     rng = np.random.default_rng(3)
     tickets = []
     for i, e in enumerate(evs):
         tickets.append(srv.submit(e.packed()))
-        if i % 5 != 4:                      # bursts of five, then a pause
+        if i < n_burst or i % 5 != 4:       # one long burst, then bursts of five and pauses
             continue
         time.sleep(float(rng.uniform(0.0, 0.05)))
     batch_sizes = []
@@ -71,6 +74,7 @@ def test_served_results_equal_alone(trk):
     c = srv.counts()
     assert c["events"] == len(evs) and c["failed"] == 0 and c["queued"] == 0
     assert max(batch_sizes) > 1, batch_sizes        # some events shared a batch
+    assert batch_sizes[-1] == 1, batch_sizes        # a short queue runs one event per call
     srv.close()
 
 
