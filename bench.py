@@ -35,35 +35,34 @@ BATCH_WORKLOAD = "barrel10_batch256"
 # flips and integer work do not count.
 #   every enumerated triplet: the curvature test (4 differences, D, |v|^2, |w|^2, 3 products,
 #     1 comparison; the pair's own terms are computed once per pair) = 14;
-#   every survivor of it: the transverse pre-fit (differences, compensated determinants,
-#     circle, q/pT and d0 with their widened range tests, perigee) = 80, and the
-#     conservative longitudinal bound (three arcs by the truncated series with their error
-#     terms and direction tests = 3 x 33, interval least squares for cot and z0 = 89, set-up
-#     = 9) = 197;
-#   every survivor of the bound: the exact transverse fit = 65, the exact longitudinal fit
-#     (first arc 17, two hit-to-hit arcs with the turn choice 2 x 46, least-squares line and
-#     range tests 37) = 146, phi0 and the five bin indices = 31.
+#   every survivor of it: the transverse fit (differences, compensated determinants,
+#     circle, q/pT and d0 with their range tests, perigee) = 65;
+#   every triplet with q/pT and d0 in range: the longitudinal fit (first arc 17, two
+#     hit-to-hit arcs with the turn choice 2 x 46, least-squares line and range tests 37)
+#     = 146;
+#   every accepted triplet: phi0 and the five bin indices = 31.
+# An arcsine or arctangent counts 1 (each is a polynomial of 8 fused multiply-adds here).
 OPS_PER_TRIPLET = 14
-OPS_PER_FIT = 80 + 197
-OPS_PER_EXACT = 65 + 146 + 31
+OPS_PER_FIT = 65
+OPS_PER_EXACT = 146
+OPS_PER_VOTE = 31
 # The method's own work, independent of how the kernel prunes (the roofline's `achieved`):
 # every enumerated triplet needs the determinant, the three squared distances and the
 # curvature comparison before it can be rejected (the 14 above) plus the reciprocal and
 # the products of the q/pT range test, about 31 operations; every accepted triplet needs
-# the whole exact fit, phi0 and the five bins, the 242 of the exact path above.
+# the whole fit, phi0 and the five bins, 65 + 146 + 31 = 242.
 METHOD_OPS_PER_TRIPLET = 31
 METHOD_OPS_PER_VOTE = 65 + 146 + 31
-# Of those, the operations that go to the special-function (MUFU) pipe, the co-bound
-# (16 per SM per clock): square roots, reciprocal square roots, reciprocals, divisions,
-# arcsines and arctangents.
-#   every survivor of the curvature test: the pre-fit's 2 square roots and 4 reciprocals,
-#     the bound's reciprocal of |c|, 2 square roots per arc and the 2 square roots and 2
-#     reciprocals of the interval line = 17;
-#   every survivor of the bound: the exact transverse fit's 2 square roots and 4 divisions,
-#     the longitudinal fit's 1 reciprocal, 8 square roots, 3 arcsines and 1 division, and
-#     phi0's arctangent = 20.
-MUFU_PER_FIT = 6 + 11
-MUFU_PER_EXACT = 6 + 13 + 1
+# Of those, the operations that go to the special-function (MUFU) pipe (16 per SM per
+# clock): square roots and reciprocals (one MUFU operation each):
+#   every survivor of the curvature test: the transverse fit's 2 square roots and 4
+#     reciprocals = 6;
+#   every triplet through the longitudinal fit: 1 reciprocal of |c|, 7 square roots and
+#     the slope's reciprocal = 9;
+#   every accepted triplet: the arctangent's reciprocal = 1.
+MUFU_PER_FIT = 6
+MUFU_PER_EXACT = 9
+MUFU_PER_VOTE = 1
 
 
 def parse():
@@ -342,7 +341,7 @@ def main():
     # FP32 lane-operation peak: 128 FP32 lanes per SM per clock
     alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12
     kernel_ops = (OPS_PER_TRIPLET * stats["n_triplets"] + OPS_PER_FIT * stats["n_fit"] +
-                  OPS_PER_EXACT * stats["n_exact"]) / 1e12
+                  OPS_PER_EXACT * stats["n_exact"] + OPS_PER_VOTE * stats["n_votes"]) / 1e12
     method_ops = (METHOD_OPS_PER_TRIPLET * stats["n_triplets"] +
                   METHOD_OPS_PER_VOTE * stats["n_votes"]) / 1e12
     achieved = method_ops / (vote_ms / 1000.0) if vote_ms else None
@@ -350,7 +349,8 @@ def main():
     hbm_peak = peaks.get("hbm_gbs")
     nbins = int(rec.lib.trk_histogram_size(rec.h))
     mufu_peak = sm_count * 16 * sm_mhz * 1e6 / 1e12
-    mufu_ops = (MUFU_PER_FIT * stats["n_fit"] + MUFU_PER_EXACT * stats["n_exact"]) / 1e12
+    mufu_ops = (MUFU_PER_FIT * stats["n_fit"] + MUFU_PER_EXACT * stats["n_exact"] +
+                MUFU_PER_VOTE * stats["n_votes"]) / 1e12
     mufu = mufu_ops / (vote_ms / 1000.0) if vote_ms else None
     line = {
         "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world,
@@ -374,15 +374,16 @@ def main():
                                        % (METHOD_OPS_PER_TRIPLET, METHOD_OPS_PER_VOTE),
                      "peak_source": "derived (SM count x lanes x sampled clock)",
                      "issue_frac": (kernel_rate / alu_peak) if kernel_rate else None,
-                     "issue_basis": "the operations the kernel executes by design, pruning "
-                                    "included: %d per enumerated triplet + %d per curvature "
-                                    "survivor + %d per exact fit"
-                                    % (OPS_PER_TRIPLET, OPS_PER_FIT, OPS_PER_EXACT),
+                     "issue_basis": "the operations the kernel executes by design: %d per "
+                                    "enumerated triplet + %d per curvature survivor + %d per "
+                                    "triplet with q/pT and d0 in range + %d per vote"
+                                    % (OPS_PER_TRIPLET, OPS_PER_FIT, OPS_PER_EXACT, OPS_PER_VOTE),
                      "mufu": {"achieved": mufu, "peak": mufu_peak, "unit": "T ops/s",
                               "frac": (mufu / mufu_peak) if mufu else None,
-                              "basis": "%d special-function ops per fit + %d per exact fit; "
-                                       "%d SMs x 16 per clock" % (MUFU_PER_FIT, MUFU_PER_EXACT,
-                                                                  sm_count)}},
+                              "basis": "%d special-function ops per curvature survivor + %d "
+                                       "per longitudinal fit + %d per vote; %d SMs x 16 per "
+                                       "clock" % (MUFU_PER_FIT, MUFU_PER_EXACT, MUFU_PER_VOTE,
+                                                  sm_count)}},
         "e2e": {"value": world * args.steps / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "stage_ms": stage_ms,
@@ -687,11 +688,9 @@ LAUNCHES_PER_CALL = 1 + 1 + 1 + 3 + 9 + 1 + 2 + 1 + 1 + 1
 # only while the vote-kernel sources hash to the recorded digest, and the traffic is
 # reported as null for a tuning without a record.
 VOTE_TRAFFIC = {"workload": "barrel10_500trk",
-                "sources_sha256": "708aa24aca5c591c2ba8810a343156a6f06e5b88d6fea6b81552a4ccb64eba04",
-                "records": [{"tile_i": 8, "tile_j": 16, "vote_level": 4,
-                             "bytes": 1.11732864e9 + 3.241699072e9},
-                            {"tile_i": 16, "tile_j": 8, "vote_level": 4,
-                             "bytes": 1.115576832e9 + 3.240372736e9}]}
+                "sources_sha256": "e4aaa436c242db35ebb528e608eab1ca7e0f7bd60532718bbc611dd778550853",
+                "records": [{"tile_i": 16, "tile_j": 8, "vote_level": 4,
+                             "bytes": 1.119124736e9 + 3.09147904e9}]}
 VOTE_SOURCES = ["trk_common.cuh", "trk_vote_kernel.cuh", "trk_vote.cu", "trk_vote_l2.cu",
                 "trk_vote_l3.cu", "trk_vote_l4.cu"]
 

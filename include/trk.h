@@ -102,7 +102,8 @@ typedef struct trk_options {
     int64_t peak_scratch_bytes;             /* scratch of the peak filter (4 B x bins per
                                                event of a pass) */
     int32_t tile_i, tile_j;                 /* pair tile of the vote kernel (one block):
-                                               16x16, 8x16, 16x8, 8x8 or 4x16 */
+                                               16x16, 8x16, 16x8, 8x8, 4x16, or the one-warp
+                                               tiles 8x4 and 4x8 */
     int32_t k_chunk;                        /* outer-layer hits staged per shared chunk */
     int32_t blocks_per_sm;                  /* persistent vote blocks per SM (0: auto) */
     int32_t use_graph;                      /* capture each call shape in a CUDA graph (the
@@ -182,9 +183,10 @@ typedef struct trk_candidates {
 /* Counters of the last call. */
 typedef struct trk_stats {
     int64_t n_triplets;                     /* sum over events and triples of |La||Lb||Lc| */
-    int64_t n_fit;                          /* triplets through the pre-test (survivors of
+    int64_t n_fit;                          /* triplets through the FP32 fit (survivors of
                                                the curvature prefilter) */
-    int64_t n_exact;                        /* triplets through the exact FP32 fit */
+    int64_t n_exact;                        /* of those, triplets whose q/pT and d0 are in
+                                               range (through the longitudinal part) */
     int64_t n_votes;                        /* accepted triplets */
     int64_t n_fp64;                         /* fits redone in FP64 */
     int64_t n_candidates;
@@ -272,9 +274,7 @@ int trk_get_votes(trk_ctx *h, int32_t *dst, uint32_t *bins, int64_t cap, int64_t
  * ijk[3t..3t+2] are indices into hits[0 .. n_hits) (DEVICE).  Writes params[5t..5t+4]
  * (FP32, NaN when degenerate), bins[t] (valid when accepted) and flags[t]: bit 0
  * accepted, bit 1 computed in FP64, bit 2 degenerate, bit 3 index out of range (nothing
- * else written for that triplet), bit 4 dropped by the vote kernel's conservative pre-test
- * (never set for a triplet the exact fit accepts: the vote kernel would lose its vote).
- * All DEVICE buffers.  Asynchronous. */
+ * else written for that triplet).  All DEVICE buffers.  Asynchronous. */
 int trk_fit_triplets(trk_ctx *h, const trk_hit *hits, int64_t n_hits, const int32_t *ijk,
                      int64_t n, float *params, uint32_t *bins, int32_t *flags, void *stream);
 
@@ -290,14 +290,15 @@ int trk_profile_stages(trk_ctx *h, float ms[8], void *stream);
  * transfer with the current one's processing (Sec. 8).  A server keeps n_lanes complete
  * handles resident (each with its own pools, stream and graphs, created with
  * lane_options) and a host queue of submitted events.  Each lane runs on its own host
- * thread.  The lanes take the GPU in turn: the lane that gets it admits waiting events,
- * in arrival order, while they fit its capacities (lane_options.max_events events,
- * max_hits hits, and the device memory of its vote list) and the backlog (one event more
- * than the first per 24 waiting: batching delays every event of a batch to its end and
- * pays only when many wait), reconstructs them in one call, and hands the GPU on as
- * soon as the kernels are done; it then copies the candidates back and files each event's
- * results while the next batch computes.  An event's results are identical whether it is
- * reconstructed alone, in a batch or by the server. */
+ * thread.  A free lane admits waiting events, in arrival order, while they fit its
+ * capacities (lane_options.max_events events, max_hits hits, and the device memory of its
+ * vote list) and the backlog (one event more than the first per 24 waiting: batching
+ * delays every event of a batch to its end and pays only when many wait), and copies them
+ * to the device while another lane computes.  The lanes take the GPU in turn: a lane
+ * holds it from launching its call until the kernels are done, then copies the
+ * candidates back and files each event's results while the next batch computes.  An
+ * event's results are identical whether it is reconstructed alone, in a batch or by the
+ * server. */
 typedef struct trk_server trk_server;
 
 typedef struct trk_served_event {

@@ -44,7 +44,7 @@ cudaError_t launch_cand_emit(const uint32_t *cbits, const uint32_t *wprefix, int
 cudaError_t launch_vote_offsets(const trk_candidate *cand, const unsigned long long *n_cand,
                                 int64_t cand_cap, int64_t *vote_off, int64_t *bsum,
                                 unsigned long long *total, cudaStream_t s);
-cudaError_t launch_assign(const AssignArgs &A, int n_sm, cudaStream_t s);
+cudaError_t launch_assign(const AssignArgs &A, int n_events, int n_sm, cudaStream_t s);
 cudaError_t launch_cand_fit(const trk_candidate *cand, const unsigned long long *n_cand,
                             int64_t cand_cap, const int32_t *hit_ids, int64_t hit_cap,
                             const CallArgs *args, double kB, int n_layers, trk_track *out,
@@ -111,7 +111,7 @@ struct trk_ctx {
     int32_t *d_m3 = nullptr;
     unsigned long long *d_ties = nullptr;
     uint32_t *d_cbits = nullptr;
-    uint32_t *d_filter = nullptr;        // candidate filter (kFilterWords)
+    uint32_t *d_filter = nullptr;        // candidate filters (kFilterWords per event)
     uint32_t *d_wprefix = nullptr;
     int64_t *d_bsum = nullptr;
     trk_candidate *d_cand = nullptr;
@@ -480,7 +480,7 @@ extern "C" int trk_create(trk_ctx **out, const trk_geometry *geometry, const trk
     ALLOC(d_m3, (int64_t)h->group * h->nbins);
     ALLOC(d_ties, h->tie_cap);
     ALLOC(d_cbits, E * h->W);
-    ALLOC(d_filter, (int64_t)kFilterWords);
+    ALLOC(d_filter, (int64_t)kFilterWords * o.max_events);
     ALLOC(d_wprefix, E * h->W);
     ALLOC(d_bsum, h->bsum_cap);
     ALLOC(d_cand, o.cand_capacity);
@@ -591,7 +591,7 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     TRK_CUDA(h, launch_vote(va, o.tile_i, o.tile_j, h->level, h->vote_grid, s));
     TRK_CUDA(h, mark(h->ev_st[1]));
     TRK_CUDA(h, cudaMemsetAsync(h->d_cbits, 0, sizeof(uint32_t) * (size_t)n_words, s));
-    TRK_CUDA(h, cudaMemsetAsync(h->d_filter, 0, sizeof(uint32_t) * kFilterWords, s));
+    TRK_CUDA(h, cudaMemsetAsync(h->d_filter, 0, sizeof(uint32_t) * kFilterWords * n_events, s));
     for (int g0 = 0; g0 < n_events; g0 += h->group) {
         const int G = (n_events - g0) < h->group ? (n_events - g0) : h->group;
         TRK_CUDA(h, launch_peaks(h->d_hist, h->d_m3, h->C, g0, G, h->td, h->bin.threshold,
@@ -639,7 +639,7 @@ static int enqueue(trk_ctx *h, int n_events, cudaStream_t s, bool capturing)
     aa.ctr = ctr;
     aa.ti = o.tile_i;
     aa.tj = o.tile_j;
-    TRK_CUDA(h, launch_assign(aa, h->n_sm, s));
+    TRK_CUDA(h, launch_assign(aa, n_events, h->n_sm, s));
     TRK_CUDA(h, launch_cand_hits(h->d_cand, &ctr->n_cand, o.cand_capacity, h->d_vote_off,
                                  h->d_assign, o.assign_capacity, h->d_args, h->d_nhits,
                                  h->max_words, h->n_sm, s));
@@ -978,7 +978,7 @@ extern "C" int trk_autotune(trk_ctx *h, const trk_hit *hits, int64_t n_hits,
 {
     if (!h || !best || reps < 1)
         return TRK_ERR_INVALID;
-    static const int tiles[][2] = {{16, 16}, {8, 16}, {16, 8}, {8, 8}, {4, 16}};
+    static const int tiles[][2] = {{16, 16}, {8, 16}, {16, 8}, {8, 8}, {4, 16}, {8, 4}, {4, 8}};
     const int levels[] = {2, 3, 4};
     trk_tuning cur;
     std::memset(&cur, 0, sizeof(cur));

@@ -115,10 +115,12 @@ struct VoteArgs {
 };
 
 // Arguments of the assignment kernels.
-// Candidate filter: a one-hash Bloom filter of the candidate (event, bin) keys, sized to
-// sit in one block's shared memory, that lets the assignment skip the random lookup in the
-// candidate bitmap for most votes.  A set bit may be a false positive; a candidate's bit
-// is always set, so the filter never drops a candidate vote.
+// Candidate filter: per event, a one-hash Bloom filter of the event's candidate bins, sized
+// to sit in one block's shared memory, that lets the assignment skip the random lookup in
+// the candidate bitmap for most votes.  A set bit may be a false positive; a candidate's
+// bit is always set, so the filter never drops a candidate vote.  A one-event call keeps
+// its filter in shared memory; a batch reads the per-event filters (192 KB each, in L2)
+// from global memory, so that the false-positive rate does not grow with the batch.
 constexpr uint32_t kFilterBits = 192u * 1024u * 8u;
 constexpr uint32_t kFilterWords = kFilterBits / 32u;
 
@@ -401,158 +403,6 @@ __device__ __forceinline__ int fit_transverse(const float4 &p1, const float4 &p2
     t.px = t.cx * f;
     t.py = t.cy * f;
     return kPass;
-}
-
-// arcsin(x) / x through the x^6 term of its series: 1 + x^2/6 + 3x^4/40 + 5x^6/112.  The
-// remaining terms are positive and below 0.075 x^8 for x <= 0.71 (the ratio of the
-// remainder to x^8 increases with x and is 0.0750 at x = 0.7).
-template <class V>
-__device__ __forceinline__ V asin_over_x_series(V x2)
-{
-    return vfma(x2, vfma(x2, vfma(x2, bc<V>(5.0f / 112.0f), bc<V>(3.0f / 40.0f)),
-                         bc<V>(1.0f / 6.0f)),
-                bc<V>(1.0f));
-}
-
-// Range test widened by 1e-4 of the range width and of |p|: for the pre-tests below,
-// whose values carry a few 1e-7 of relative error.
-__device__ __forceinline__ bool in_range_loose(const FitConst &C, int k, float p)
-{
-    const float m = 1e-4f * (C.hi[k] - C.lo[k] + fabsf(p));
-    return p >= C.lo[k] - m && p < C.hi[k] + m;
-}
-
-// The transverse fit of fit_transverse for the pre-test: the same arithmetic with the q/pT
-// and d0 range tests widened by 1e-4, so it passes every triplet that fit_transverse
-// passes.  The FP64 trigger is computed exactly as there.
-__device__ __forceinline__ int fit_transverse_bound(const float4 &p1, const float4 &p2,
-                                                    const float4 &p3, const FitConst &C, Trans &t)
-{
-    t.ux = p2.x - p1.x;
-    t.uy = p2.y - p1.y;
-    t.vx = p3.x - p1.x;
-    t.vy = p3.y - p1.y;
-    const float wx = p3.x - p2.x, wy = p3.y - p2.y;
-    const float D = det2(t.ux, t.uy, t.vx, t.vy);
-    t.uu = fmaf(t.ux, t.ux, t.uy * t.uy);
-    t.vv = fmaf(t.vx, t.vx, t.vy * t.vy);
-    const float ww = fmaf(wx, wx, wy * wy);
-    if (D * D <= C.sag2 * t.vv)
-        return kNeedFp64;
-    const float sq = approx_sqrt(t.uu * t.vv * ww);
-    const float rq = approx_rcp(sq);
-    t.qopt = (-2.0f * D) * rq * C.inv_kB;
-    if (!in_range_loose(C, 1, t.qopt))
-        return kReject;
-    const float inv2d = 0.5f * approx_rcp(D);
-    t.cpx = det2(t.vy, t.uy, t.vv, t.uu) * inv2d;
-    t.cpy = det2(t.ux, t.vx, t.uu, t.vv) * inv2d;
-    t.cx = p1.x + t.cpx;
-    t.cy = p1.y + t.cpy;
-    t.R = sq * fabsf(inv2d);
-    t.inv2r = fabsf(D) * rq;
-    t.cn = approx_sqrt(fmaf(t.cx, t.cx, t.cy * t.cy));
-    const float power = fmaf(p1.x, p1.x, p1.y * p1.y) + 2.0f * fmaf(p1.x, t.cpx, p1.y * t.cpy);
-    const float dist = power * approx_rcp(t.cn + t.R);
-    t.sgn = D > 0.0f ? 1.0f : -1.0f;
-    t.d0 = t.sgn * dist;
-    if (!in_range_loose(C, 2, t.d0))
-        return kReject;
-    if (!(t.cn > 0.0f) || !(t.R < 3.0e37f))
-        return kNeedFp64;
-    const float f = dist * approx_rcp(t.cn);
-    t.px = t.cx * f;
-    t.py = t.cy * f;
-    return kPass;
-}
-
-// Signed path length from the perigee to hit(s) (hx, hy), bounded without
-// transcendentals: |s| from a truncated arcsine series -- chord / 2R = x <= 0.7: chord
-// (series of x); beyond, the complementary form R (pi - 2 y series(y)) with
-// y = |(P - c) + (p - c)| / 2R, (bx, by) = p - c -- and E, a rigorous bound on its error
-// (series truncation, FP32 evaluation, and the sign when the direction from P is not
-// resolved).  (ax, ay) = P - c.
-template <class V>
-__device__ __forceinline__ void arc_bound(V hx, V hy, V bx, V by, V ax, V ay, const Trans &t,
-                                          V &sh, V &E)
-{
-    const V dx = vsub(hx, bc<V>(t.px)), dy = vsub(hy, bc<V>(t.py));
-    const V ch = approx_sqrt(vfma(dx, dx, vmul(dy, dy)));
-    const V x = vmul(ch, bc<V>(t.inv2r));
-    // both forms share 2R a series(a^2) with a = x (near) or y (far), and the same
-    // truncation bound 2R a 0.075 a^8; evaluated without a branch (lanes differ)
-    const V sx = vadd(ax, bx), sy = vadd(ay, by);
-    const V y = vmin(vmul(approx_sqrt(vfma(sx, sx, vmul(sy, sy))), bc<V>(t.inv2r)), bc<V>(1.0f));
-    const auto far = vnot(vle(x, bc<V>(0.7f)));
-    const V a = vsel(far, y, x);
-    const V a2 = vmul(a, a), a4 = vmul(a2, a2);
-    const V twoRa = vmul(bc<V>(2.0f * t.R), a);
-    const V arc = vmul(twoRa, asin_over_x_series(a2));
-    const V mag = vsel(far, vfma(bc<V>(t.R), bc<V>(3.14159265f), vneg(arc)), arc);
-    V e = vmul(twoRa, vmul(vmul(bc<V>(0.075f), a4), a4));
-    e = vadd(e, vfma(bc<V>(4e-6f), mag, bc<V>(1e-6f * t.R)));
-    const V pr = det2v(dx, dy, bc<V>(t.cx), bc<V>(t.cy));
-    // direction from P not resolved: either sign
-    const V lim = vmul(vmul(bc<V>(1e-3f), ch), bc<V>(t.cn));
-    e = vsel(vle(vabs(pr), lim), vadd(e, vmul(bc<V>(2.0f), mag)), e);
-    sh = vsel(vge(vmul(bc<V>(t.sgn), pr), bc<V>(0.0f)), mag, vneg(mag));
-    E = e;
-}
-
-// Conservative longitudinal test without transcendentals: may the triplet's (cot, z0) be
-// in range?  Each s_k is bounded by arc_bound (hits 1 and 2 as a pair, hit 3 alone), and
-// interval arithmetic runs over the least-squares line.  false = certainly outside the
-// cot or z0 range (the exact fit would reject it).
-__device__ __forceinline__ bool z_may_accept(const float4 &p1, const float4 &p2, const float4 &p3,
-                                             const Trans &t, const FitConst &C)
-{
-    const float rcn = approx_rcp(t.cn);
-    const float ax = -t.R * t.cx * rcn, ay = -t.R * t.cy * rcn;          // P - c
-    float sh[3], E[3];
-    {
-        float2 s2, e2;
-        arc_bound(make_float2(p1.x, p2.x), make_float2(p1.y, p2.y),
-                  make_float2(-t.cpx, t.ux - t.cpx), make_float2(-t.cpy, t.uy - t.cpy),
-                  make_float2(ax, ax), make_float2(ay, ay), t, s2, e2);
-        sh[0] = s2.x;
-        sh[1] = s2.y;
-        E[0] = e2.x;
-        E[1] = e2.y;
-    }
-    arc_bound(p3.x, p3.y, t.vx - t.cpx, t.vy - t.cpy, ax, ay, t, sh[2], E[2]);
-    const float zbar = (p1.z + p2.z + p3.z) * (1.0f / 3.0f);
-    const float sbar = (sh[0] + sh[1] + sh[2]) * (1.0f / 3.0f);
-    const float eb = (E[0] + E[1] + E[2]) * (1.0f / 3.0f);
-    const float t0 = sh[0] - sbar, t1 = sh[1] - sbar, t2 = sh[2] - sbar;
-    const float z0d = p1.z - zbar, z1d = p2.z - zbar, z2d = p3.z - zbar;
-    const float d0 = E[0] + eb, d1 = E[1] + eb, d2 = E[2] + eb;   // bound of each |dt_k|
-    const float T = fmaf(t0, t0, fmaf(t1, t1, t2 * t2));
-    const float Z = fmaf(t0, z0d, fmaf(t1, z1d, t2 * z2d));
-    const float dZ = fmaf(d0, fabsf(z0d), fmaf(d1, fabsf(z1d), d2 * fabsf(z2d)));
-    const float nd = approx_sqrt(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
-    const float rt = approx_sqrt(T);
-    if (!(rt > 2.0f * nd))
-        return true;
-    const float tlo = (rt - nd) * (rt - nd), thi = (rt + nd) * (rt + nd);
-    const float zlo = Z - dZ, zhi = Z + dZ;
-    const float rlo = approx_rcp(tlo), rhi = approx_rcp(thi);
-    float clo = fminf(zlo * rlo, zlo * rhi), chi = fmaxf(zhi * rlo, zhi * rhi);
-    // FP32 margin (the exact path's own errors are far below it)
-    const float m3 = 1e-4f * fmaxf(fabsf(clo) + fabsf(chi), C.hi[3] - C.lo[3]);
-    clo -= m3;
-    chi += m3;
-    if (chi < C.lo[3] || clo >= C.hi[3])
-        return false;
-    // z0 = zbar - cot * sbar_true, sbar_true in [sbar - eb, sbar + eb]
-    const float slo = sbar - eb, shi = sbar + eb;
-    const float q0 = clo * slo, q1 = clo * shi, q2 = chi * slo, q3 = chi * shi;
-    const float plo = fminf(fminf(q0, q1), fminf(q2, q3));
-    const float phi = fmaxf(fmaxf(q0, q1), fmaxf(q2, q3));
-    float zlo0 = zbar - phi, zhi0 = zbar - plo;
-    const float m4 = 1e-4f * fmaxf(fabsf(zlo0) + fabsf(zhi0) + fabsf(zbar), C.hi[4] - C.lo[4]);
-    zlo0 -= m4;
-    zhi0 += m4;
-    return !(zhi0 < C.lo[4] || zlo0 >= C.hi[4]);
 }
 
 // Central angle (0 .. pi) of the arc from P to a hit `chord` away, with `sumlen` the

@@ -231,7 +231,7 @@ __device__ __forceinline__ void set_candidate(uint32_t *cbits, int64_t W, uint32
     atomicOr(&cbits[(size_t)e * W + (bin >> 5)], 1u << (bin & 31));
     if (filter) {
         const uint32_t fb = cand_filter_bit(e, bin);
-        atomicOr(&filter[fb >> 5], 1u << (fb & 31));
+        atomicOr(&filter[(size_t)e * kFilterWords + (fb >> 5)], 1u << (fb & 31));
     }
 }
 
@@ -328,6 +328,99 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_pass1(const int32_t *hist
     }
 }
 
+// Pass 1 in registers, for row blocks of at most 32 cot lines of 4, 8, 12 or 16 z0 bins
+// (16-byte aligned histogram): a warp per (event, phi0, q/pT, run of kRun1 d0 rows), a
+// lane per cot line holding the line's z0 bins.  Per d0 row the lane loads its line (16-byte
+// loads; the warp reads the row's contiguous n3 n4 counts), combines over z0 within its
+// registers and over cot with the neighbouring lanes (shuffles), and slides a window of
+// three rows along d0, storing the middle row.  No shared memory and no barriers; every
+// count is read once plus two halo rows per run.
+constexpr int kRun1 = 8;
+constexpr int kPass1WarpsPerBlock = 4;
+
+template <int N4>
+__global__ void __launch_bounds__(32 * kPass1WarpsPerBlock)
+    k_peak_pass1r(const int32_t *hist, int32_t *m3, FitConst C, int g0, int G,
+                  const int32_t *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int n0 = C.n[0], n1 = C.n[1], n2 = C.n[2], n3 = C.n[3];
+    const int runs = (n2 + kRun1 - 1) / kRun1;
+    int64_t w = (int64_t)blockIdx.x * kPass1WarpsPerBlock + (threadIdx.x >> 5);
+    if (w >= (int64_t)G * n0 * n1 * runs)
+        return;
+    const int run = (int)(w % runs);
+    w /= runs;
+    const int i1 = (int)(w % n1);
+    w /= n1;
+    const int i0 = (int)(w % n0);
+    const int ge = (int)(w / n0);
+    const int e = g0 + ge;
+    if (status[e] != 0)
+        return;
+    const bool line = lane < n3;
+    const uint32_t plane = C.stride[2];
+    const uint32_t base = (uint32_t)i0 * C.stride[0] + (uint32_t)i1 * C.stride[1] +
+                          (uint32_t)lane * N4;
+    const int32_t *h_e = hist + (size_t)e * C.nbins + base;
+    int32_t *out = m3 + (size_t)ge * C.nbins + base;
+    constexpr int NV = N4 / 4;
+    // keys of row d combined over z0 and cot (0 outside the histogram)
+    auto row_keys = [&](int d, int (&b)[N4]) {
+        int k[N4];
+        if (line && d >= 0 && d < n2) {
+            const int4 *q = reinterpret_cast<const int4 *>(h_e + (size_t)d * plane);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const int4 x = __ldg(q + v);
+                k[4 * v] = x.x << 1;
+                k[4 * v + 1] = x.y << 1;
+                k[4 * v + 2] = x.z << 1;
+                k[4 * v + 3] = x.w << 1;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < N4; ++j)
+                k[j] = 0;
+        }
+        int a[N4];
+#pragma unroll
+        for (int j = 0; j < N4; ++j)
+            a[j] = kcomb3(j > 0 ? k[j - 1] : 0, k[j], j + 1 < N4 ? k[j + 1] : 0);
+#pragma unroll
+        for (int j = 0; j < N4; ++j) {
+            int up = __shfl_up_sync(kFull, a[j], 1);
+            int dn = __shfl_down_sync(kFull, a[j], 1);
+            up = lane > 0 ? up : 0;
+            dn = lane + 1 < n3 ? dn : 0;
+            b[j] = kcomb3(up, a[j], dn);
+        }
+    };
+    const int d_start = run * kRun1;
+    const int d_end = min(n2, d_start + kRun1);
+    int prev[N4], cur[N4];
+    row_keys(d_start - 1, prev);
+    row_keys(d_start, cur);
+    for (int d = d_start; d < d_end; ++d) {
+        int nx[N4];
+        row_keys(d + 1, nx);
+        if (line) {
+            int4 *o = reinterpret_cast<int4 *>(out + (size_t)d * plane);
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                o[v] = make_int4(kcomb3(prev[4 * v], cur[4 * v], nx[4 * v]),
+                                 kcomb3(prev[4 * v + 1], cur[4 * v + 1], nx[4 * v + 1]),
+                                 kcomb3(prev[4 * v + 2], cur[4 * v + 2], nx[4 * v + 2]),
+                                 kcomb3(prev[4 * v + 3], cur[4 * v + 3], nx[4 * v + 3]));
+        }
+#pragma unroll
+        for (int j = 0; j < N4; ++j) {
+            prev[j] = cur[j];
+            cur[j] = nx[j];
+        }
+    }
+}
+
 // Pass 2: thread per (event, q/pT row, V consecutive inner positions, segment of kSeg
 // phi0 rows); walks its segment keeping the maxima over q/pT +-1 of the three phi0 rows
 // around the current one.  Segments (two extra rows of loads per kSeg) give the grid
@@ -375,7 +468,7 @@ __device__ __forceinline__ IntV<V> vcomb(IntV<V> a, const IntV<V> &b)
 }
 
 template <int V>
-__global__ void __launch_bounds__(kPeakThreads) k_peak_pass2(const int32_t *hist, const int32_t *m3,
+__global__ void __launch_bounds__(kPeakThreads, 3) k_peak_pass2(const int32_t *hist, const int32_t *m3,
                                                              FitConst C, int g0, int G,
                                                              int threshold, const int32_t *status,
                                                              uint32_t *cbits, int64_t W,
@@ -648,75 +741,61 @@ __device__ __forceinline__ ItemLoc locate_item(int64_t item, const int64_t *item
 constexpr int kAssignThreads = 1024;
 
 // Assignment, part 1: a stream over the bins of the vote list that finds the candidate
-// votes and queues their slots.  Only ~1 % of the votes land in candidate bins, so each
-// thread takes kP groups of four adjacent slots (one 16-byte load each; a warp covers four
-// whole 32-slot chunks) a grid stride apart and issues their bin, chunk count and chunk
-// event loads together; bins are read once, with the streaming (evict-first) hint.  Slots
-// past a chunk's count hold stale data and are discarded.  The shared-memory candidate
-// filter leaves the bitmap lookup to the few votes whose filter bit is set.  A candidate
-// vote's slot goes to the queue with one atomic per warp, so the stream never waits on the
-// dependent loads of the hit decoding (part 2).
+// votes and queues their slots.  Only ~1 % of the votes land in candidate bins.  A warp
+// takes kU whole 32-slot chunks at a time, a lane per slot: every lane issues its kU bin
+// loads (each warp load is one chunk's 128 contiguous bytes, streamed with the evict-first
+// hint) while the chunks' counts and events arrive as warp-wide broadcasts; slots past a
+// chunk's count hold stale data and are discarded.  The shared-memory candidate filter
+// leaves the bitmap lookup to the few votes whose filter bit is set, and those lookups are
+// issued together.  A candidate vote's slot goes to the queue with one atomic per warp, so
+// the stream never waits on the dependent loads of the hit decoding (part 2).
+template <bool kOneEvent>
 __global__ void __launch_bounds__(kAssignThreads, 1) k_assign_scan(AssignArgs A)
 {
     extern __shared__ uint32_t s_filter[];
-    for (uint32_t q = threadIdx.x; q < kFilterWords / 4; q += kAssignThreads)
-        reinterpret_cast<uint4 *>(s_filter)[q] = __ldg(reinterpret_cast<const uint4 *>(A.filter) + q);
-    __syncthreads();
+    if (kOneEvent) {
+        for (uint32_t q = threadIdx.x; q < kFilterWords / 4; q += kAssignThreads)
+            reinterpret_cast<uint4 *>(s_filter)[q] =
+                __ldg(reinterpret_cast<const uint4 *>(A.filter) + q);
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     int64_t n_chunks = (int64_t)A.ctr->n_chunks;
     n_chunks = n_chunks < A.chunk_cap ? n_chunks : A.chunk_cap;
-    const int64_t n_slots = n_chunks * kWarp;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    constexpr int kP = 4, kU = 4 * kP;
-    const int64_t n_quads = n_slots / 4;
-    // warp-uniform trip count (the queue append is warp-collective)
-    const int64_t q_warp0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31);
-    for (int64_t qw = q_warp0; qw < n_quads; qw += kP * stride) {
-        const int64_t q0 = qw + lane;
+    constexpr int kU = 16;
+    const int64_t warps = (int64_t)gridDim.x * (kAssignThreads / 32);
+    const int64_t warp = blockIdx.x * (int64_t)(kAssignThreads / 32) + (threadIdx.x >> 5);
+    for (int64_t c0 = warp; c0 < n_chunks; c0 += kU * warps) {
         uint32_t bin[kU];
-        int ev[kP];
-        int cnt[kP];
+        int cnt[kU], ev[kU];
 #pragma unroll
-        for (int u = 0; u < kP; ++u) {
-            const int64_t qd = q0 + u * stride;
-            const bool in = qd < n_quads;
-            uint4 four = make_uint4(0u, 0u, 0u, 0u);
-            if (in)
-                four = __ldcs(reinterpret_cast<const uint4 *>(A.vote_bin) + qd);
-            bin[4 * u] = four.x;
-            bin[4 * u + 1] = four.y;
-            bin[4 * u + 2] = four.z;
-            bin[4 * u + 3] = four.w;
-            cnt[u] = in ? __ldg(A.chunk_count + (qd >> 3)) : 0;
-            ev[u] = in ? __ldg(A.chunk_event + (qd >> 3)) : 0;
+        for (int u = 0; u < kU; ++u) {
+            const int64_t c = c0 + u * warps;
+            const bool in = c < n_chunks;
+            bin[u] = in ? __ldcs(A.vote_bin + c * kWarp + lane) : 0u;
+            cnt[u] = in ? __ldg(A.chunk_count + c) : 0;
+            ev[u] = in ? __ldg(A.chunk_event + c) : 0;
         }
-        // slot within its chunk of vote r of group u: 4 (qd & 7) + r; the event's part of
-        // the filter hash and its bitmap row are taken once per group
-        const int sub = 4 * (int)(q0 & 7);
-        uint32_t maybe = 0;           // bit r: vote r is valid and passes the filter
+        uint32_t maybe = 0;           // bit u: this lane's vote of chunk u passes the filter
 #pragma unroll
-        for (int u = 0; u < kP; ++u) {
-            const int nvalid = cnt[u] - sub;
-            const uint32_t eh = (uint32_t)ev[u] * kFilterEventMul;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const uint32_t fb = cand_filter_bit_h(eh, bin[4 * u + c]);
-                const uint32_t f = (s_filter[fb >> 5] >> (fb & 31)) & 1u;
-                maybe |= (c < nvalid ? f : 0u) << (4 * u + c);
-            }
+        for (int u = 0; u < kU; ++u) {
+            const uint32_t fb = cand_filter_bit(ev[u], bin[u]);
+            const uint32_t fw = kOneEvent ? s_filter[fb >> 5]
+                                          : __ldg(A.filter + (size_t)ev[u] * kFilterWords + (fb >> 5));
+            const uint32_t f = (fw >> (fb & 31)) & 1u;
+            maybe |= (lane < cnt[u] ? f : 0u) << u;
         }
-        uint32_t mine = 0;            // bit r: vote r is a candidate vote
-        if (maybe) {
-            // all lookups issued before any is used, so that they wait together
+        uint32_t mine = 0;            // bit u: this lane's vote of chunk u is a candidate vote
+        if (__any_sync(kFull, maybe != 0)) {
             uint32_t word[kU];
 #pragma unroll
-            for (int r = 0; r < kU; ++r)
-                word[r] = ((maybe >> r) & 1u)
-                              ? __ldg(A.cbits + (size_t)ev[r >> 2] * A.W + (bin[r] >> 5))
+            for (int u = 0; u < kU; ++u)
+                word[u] = ((maybe >> u) & 1u)
+                              ? __ldg(A.cbits + (size_t)ev[u] * A.W + (bin[u] >> 5))
                               : 0u;
 #pragma unroll
-            for (int r = 0; r < kU; ++r)
-                mine |= ((word[r] >> (bin[r] & 31)) & 1u) << r;
+            for (int u = 0; u < kU; ++u)
+                mine |= ((word[u] >> (bin[u] & 31)) & 1u) << u;
         }
         const int nm = __popc(mine);
         int incl = nm;
@@ -735,10 +814,10 @@ __global__ void __launch_bounds__(kAssignThreads, 1) k_assign_scan(AssignArgs A)
         base = __shfl_sync(kFull, base, 31);
         unsigned long long pos = base + (unsigned long long)(incl - nm);
         while (mine) {
-            const int r = __ffs(mine) - 1;
+            const int u = __ffs(mine) - 1;
             mine &= mine - 1;
             if ((int64_t)pos < A.cqueue_cap)
-                A.cqueue[pos] = (unsigned long long)(4 * (q0 + (r >> 2) * stride) + (r & 3));
+                A.cqueue[pos] = (unsigned long long)((c0 + u * warps) * kWarp + lane);
             ++pos;
         }
     }
@@ -922,7 +1001,7 @@ cudaError_t prepare_pipeline_kernels()
                              200 * 1024);
     if (e != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_assign_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_assign_scan<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(uint32_t) * kFilterWords));
 }
 
@@ -956,10 +1035,32 @@ cudaError_t launch_peaks(const int32_t *hist, int32_t *m3, const FitConst &C, in
                          uint32_t *filter, unsigned long long *ties, unsigned long long *n_ties,
                          int64_t tie_cap, int n_sm, cudaStream_t s, bool vec_ok)
 {
-    const size_t sm = peak_pass1_smem(C, td);
-    const int nslab = (C.n[2] + td - 1) / td;
-    const int64_t grid1 = (int64_t)G * C.n[0] * C.n[1] * nslab;
-    k_peak_pass1<<<(unsigned)grid1, kPeakThreads, sm, s>>>(hist, m3, C, g0, td, status);
+    const bool reg1 = vec_ok && C.n[3] <= 32 && C.n[4] % 4 == 0 && C.n[4] <= 16;
+    if (reg1) {
+        const int64_t warps = (int64_t)G * C.n[0] * C.n[1] * ((C.n[2] + kRun1 - 1) / kRun1);
+        const unsigned grid1 =
+            (unsigned)((warps + kPass1WarpsPerBlock - 1) / kPass1WarpsPerBlock);
+        const unsigned bt = 32 * kPass1WarpsPerBlock;
+        switch (C.n[4]) {
+        case 4:
+            k_peak_pass1r<4><<<grid1, bt, 0, s>>>(hist, m3, C, g0, G, status);
+            break;
+        case 8:
+            k_peak_pass1r<8><<<grid1, bt, 0, s>>>(hist, m3, C, g0, G, status);
+            break;
+        case 12:
+            k_peak_pass1r<12><<<grid1, bt, 0, s>>>(hist, m3, C, g0, G, status);
+            break;
+        default:
+            k_peak_pass1r<16><<<grid1, bt, 0, s>>>(hist, m3, C, g0, G, status);
+            break;
+        }
+    } else {
+        const size_t sm = peak_pass1_smem(C, td);
+        const int nslab = (C.n[2] + td - 1) / td;
+        const int64_t grid1 = (int64_t)G * C.n[0] * C.n[1] * nslab;
+        k_peak_pass1<<<(unsigned)grid1, kPeakThreads, sm, s>>>(hist, m3, C, g0, td, status);
+    }
     const bool vec = vec_ok && (C.stride[1] % 4) == 0;
     const int64_t threads = (int64_t)G * C.n[1] * C.stride[1] / (vec ? 4 : 1) *
                             ((C.n[0] + kSeg - 1) / kSeg);
@@ -1013,10 +1114,14 @@ cudaError_t launch_vote_offsets(const trk_candidate *cand, const unsigned long l
     return scan_exclusive(CandVotes3{cand}, n_cand, 0, cand_cap, vote_off, bsum, total, s);
 }
 
-cudaError_t launch_assign(const AssignArgs &A, int n_sm, cudaStream_t s)
+cudaError_t launch_assign(const AssignArgs &A, int n_events, int n_sm, cudaStream_t s)
 {
-    // the stream: persistent, one block per SM (the filter takes most of the shared memory)
-    k_assign_scan<<<n_sm, kAssignThreads, sizeof(uint32_t) * kFilterWords, s>>>(A);
+    // the stream: persistent, one block per SM (a one-event call's filter takes most of
+    // the shared memory)
+    if (n_events == 1)
+        k_assign_scan<true><<<n_sm, kAssignThreads, sizeof(uint32_t) * kFilterWords, s>>>(A);
+    else
+        k_assign_scan<false><<<n_sm, kAssignThreads, 0, s>>>(A);
     k_assign_cvotes<<<n_sm * 8, 256, 0, s>>>(A);
     return cudaGetLastError();
 }

@@ -7,11 +7,12 @@
 // host queue; whenever a lane is free it admits the waiting events, in arrival order, that
 // fit its capacities -- events, hits, and device memory for their votes -- copies them in,
 // reconstructs them in one call and hands each event's candidates back.  The lanes take
-// the GPU in turn: a lane holds it from admitting its batch until the batch's kernels have
-// finished, then releases it and copies the results back and files them while the next
-// lane's batch computes, so the transfers and the host work of one batch overlap the
-// computation of the next, and batches do not slow each other down by sharing the GPU.
-// A lane forms its batch only when it holds the GPU, from the events that wait then.
+// the GPU in turn: a free lane forms its batch from the events waiting then, packs it and
+// queues its copy to the device while another lane's batch computes, then holds the GPU
+// from launching its kernels until they have finished, releases it, and copies the
+// results back and files them while the next lane's batch computes.  So the transfers and
+// the host work of one batch overlap the computation of another, and batches do not slow
+// each other down by sharing the GPU.
 //
 // Batch size follows the backlog.  Batching k events saves a few per cent of each event's
 // device time (fewer launches and tails; about 4 % at four events of the 256-event mix on
@@ -124,10 +125,11 @@ static void admit(trk_server *S, std::vector<Pending> &batch)
     }
 }
 
-// Computes the events `which` of `batch` on the lane's handle (the caller holds the GPU),
-// returns the call's code and outputs; the results stay on the device.
-static int compute(trk_server *S, int lane, std::vector<Pending> &batch,
-                   const std::vector<size_t> &which, trk_candidates &out)
+// Packs the events `which` of `batch` into the lane's pinned staging buffers and queues
+// their copy to the device on the lane's stream.  Needs no GPU lock: the copy overlaps the
+// kernels of the lane that holds the GPU.
+static int stage(trk_server *S, int lane, std::vector<Pending> &batch,
+                 const std::vector<size_t> &which)
 {
     trk_hit *sh = S->stage_hits[lane];
     int64_t *so = S->stage_offs[lane];
@@ -145,10 +147,16 @@ static int compute(trk_server *S, int lane, std::vector<Pending> &batch,
         cudaMemcpyAsync(S->d_offs[lane], so, sizeof(int64_t) * (size_t)(n_ev + 1),
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
         return TRK_ERR_CUDA;
+    return TRK_OK;
+}
+
+// Reconstructs the staged events (the caller holds the GPU); returns the call's code and
+// outputs once the kernels are done; the results stay on the device.
+static int compute(trk_server *S, int lane, int n_ev, trk_candidates &out)
+{
     std::memset(&out, 0, sizeof(out));
-    // returns once the kernels are done (the per-event counts are on the host)
-    return trk_reconstruct(S->ctx[lane], S->d_hits[lane], so[n_ev], S->d_offs[lane], n_ev, &out,
-                           st);
+    return trk_reconstruct(S->ctx[lane], S->d_hits[lane], S->stage_offs[lane][n_ev],
+                           S->d_offs[lane], n_ev, &out, S->streams[lane]);
 }
 
 // Copies the results back, files every event and returns the events to run again alone
@@ -246,27 +254,31 @@ static void lane_loop(trk_server *S, int lane)
         std::vector<size_t> all;
         trk_candidates out;
         int rc;
+        // a free lane forms its batch from what waits now and stages it while another
+        // lane's batch computes; it then waits for the GPU and holds it until its kernels
+        // are done
         {
-            // the GPU is this lane's from admission until its kernels are done; the batch is
-            // everything that waits when the GPU frees up
+            std::lock_guard<std::mutex> lk(S->mu);
+            admit(S, batch);
+        }
+        if (batch.empty())
+            continue;
+        all.resize(batch.size());
+        for (size_t e = 0; e < batch.size(); ++e)
+            all[e] = e;
+        rc = stage(S, lane, batch, all);
+        if (rc == TRK_OK) {
             std::lock_guard<std::mutex> g(S->gpu_mu);
-            {
-                std::lock_guard<std::mutex> lk(S->mu);
-                admit(S, batch);
-            }
-            if (batch.empty())
-                continue;
-            all.resize(batch.size());
-            for (size_t e = 0; e < batch.size(); ++e)
-                all[e] = e;
-            rc = compute(S, lane, batch, all, out);
+            rc = compute(S, lane, (int)all.size(), out);
+        } else {
+            std::memset(&out, 0, sizeof(out));
         }
         for (size_t e : deliver(S, lane, batch, all, rc, out)) {
             const std::vector<size_t> one{e};
-            int rc1;
-            {
+            int rc1 = stage(S, lane, batch, one);
+            if (rc1 == TRK_OK) {
                 std::lock_guard<std::mutex> g(S->gpu_mu);
-                rc1 = compute(S, lane, batch, one, out);
+                rc1 = compute(S, lane, 1, out);
             }
             deliver(S, lane, batch, one, rc1, out);
         }

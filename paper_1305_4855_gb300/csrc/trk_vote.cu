@@ -63,13 +63,6 @@ __global__ void k_fit_triplets(const trk_hit *hits, int64_t n_hits, const int32_
                     fl |= 1;
             }
         }
-        // the vote kernel's conservative pre-test (a vote needs it to keep the triplet)
-        {
-            Trans tb;
-            const int sb = fit_transverse_bound(p1, p2, p3, C, tb);
-            if (sb == kReject || (sb == kPass && !z_may_accept(p1, p2, p3, tb, C)))
-                fl |= 16;
-        }
         for (int k = 0; k < 5; ++k)
             params[5 * t + k] = par[k];
         bins[t] = bin;
@@ -99,7 +92,8 @@ static cudaError_t vote_dispatch(int op, int ti, int tj, int level, const VoteAr
 bool vote_tile_supported(int ti, int tj)
 {
     return (ti == 16 && tj == 16) || (ti == 8 && tj == 16) || (ti == 16 && tj == 8) ||
-           (ti == 8 && tj == 8) || (ti == 4 && tj == 16);
+           (ti == 8 && tj == 8) || (ti == 4 && tj == 16) || (ti == 8 && tj == 4) ||
+           (ti == 4 && tj == 8);
 }
 
 bool vote_level_supported(int level) { return level >= 2 && level <= 4; }

@@ -6,13 +6,13 @@
 // from a device counter.  Each thread owns one (inner, middle) hit pair and walks the
 // outer-layer hits, staged in shared memory, through three stages:
 //   A  curvature prefilter (14 FP32 ops): a superset test of the q/pT range;
-//   B  the transverse pre-fit and the conservative longitudinal bound (superset tests of
-//      the q/pT, d0, cot and z0 ranges);
-//   C  the FP32 fit itself, phi0, the five bin indices, the histogram atomic and the
-//      vote-list record.
-// Between stages the surviving (pair, hit) items are compacted into per-warp ring
-// queues in shared memory so that B and C run with all 32 lanes busy.  Fits that the
-// FP32 path cannot resolve (near-collinear, degenerate) are recomputed in FP64.
+//   B  the FP32 fit: the transverse part (q/pT, d0, with their exact range tests), then
+//      for the triplets in range the longitudinal part (cot, z0);
+//   C  phi0, the five bin indices, the histogram atomic and the vote-list record.
+// Between stages the surviving items are compacted into per-warp ring queues in shared
+// memory (stage B's accepted fits with their parameters) so that every stage runs with
+// all 32 lanes busy.  Fits that the FP32 path cannot resolve (near-collinear, degenerate)
+// are recomputed in FP64.
 #pragma once
 
 #include "trk_common.cuh"
@@ -26,12 +26,18 @@ struct Q1 {                       // a (pair, outer hit) item
     uint32_t code;                // vote_code(i in tile, j in tile, k in layer c)
 };
 
+struct __align__(16) Q2 {         // an accepted FP32 fit: everything but phi0
+    float cx, cy, sgn, qopt;
+    float d0, cot, z0;
+    uint32_t code;
+};
+
 constexpr int kRing = 64;
 
 template <int NW>
 struct WarpQueues {
     Q1 q1[NW][kRing];             // survivors of the curvature prefilter
-    Q1 q2[NW][kRing];             // survivors of the transverse fit and the z bound
+    Q2 q2[NW][kRing];             // triplets whose FP32 fit is in range
     uint64_t stg[NW][kRing];      // votes waiting for a 32-slot chunk
     int4 loc;                     // chunk_loc of the current work item
 };
@@ -98,77 +104,101 @@ __device__ __forceinline__ void push_votes(const VoteArgs &A, WarpQueues<NW> &Q,
     }
 }
 
-// Exact fit, phi0, bins and vote on up to 32 queued survivors of the bounds.
+// phi0, bins and vote on up to 32 queued accepted fits.
 template <int NW, int TJ>
 __device__ __forceinline__ void drain2(const VoteArgs &A, WarpQueues<NW> &Q, WarpState &ws, int w,
-                                       int lane, int count, const float4 *s_i, const float4 *s_j,
-                                       int32_t *hist_e, int item, int event)
+                                       int lane, int count, int32_t *hist_e, int item, int event)
 {
     __syncwarp();
     bool has = false;
-    bool f64 = false;
     uint32_t bin = 0, code = 0;
-    float4 p1, p2, p3;
     if (lane < count) {
-        const Q1 e = Q.q2[w][(ws.h2 + lane) & (kRing - 1)];
-        code = e.code;
-        p1 = s_i[code_i(code)];
-        p2 = s_j[code_j(code)];
-        p3 = make_float4(e.x, e.y, e.z, 0.0f);
+        const Q2 e = Q.q2[w][(ws.h2 + lane) & (kRing - 1)];
         FitB r;
-        const int st = fit_stage_b(p1, p2, p3, A.C, r);
-        ws.n_exact++;
-        if (st == kPass) {
-            float phi0;
-            has = fit_stage_c(r, A.C, phi0, bin);
-        } else if (st == kNeedFp64) {
-            f64 = true;
-        }
+        r.cx = e.cx;
+        r.cy = e.cy;
+        r.sgn = e.sgn;
+        r.qopt = e.qopt;
+        r.d0 = e.d0;
+        r.cot = e.cot;
+        r.z0 = e.z0;
+        code = e.code;
+        float phi0;
+        has = fit_stage_c(r, A.C, phi0, bin);
     }
     ws.h2 = (ws.h2 + count) & (kRing - 1);
     ws.n2 -= count;
-    // FP64 recomputation of the near-collinear / degenerate ones (rare)
-    if (__any_sync(kFull, f64)) {
-        if (f64) {
-            double par[5];
-            has = (fit_f64(p1, p2, p3, A.C, par, bin) == kFit64Accepted);
-            ws.n_fp64++;
-        }
-    }
     __syncwarp();
     push_votes(A, Q, ws, w, lane, has, bin, code, hist_e, item, event);
 }
 
-// Transverse fit and the longitudinal bound on up to 32 queued prefilter survivors.
+// The FP32 fit on up to 32 queued prefilter survivors: the transverse part, then the
+// longitudinal part for those whose q/pT and d0 are in range.  Accepted fits go to the
+// second queue; FP64 recomputations (rare) vote here.
 template <int NW, int TJ>
 __device__ __forceinline__ void drain1(const VoteArgs &A, WarpQueues<NW> &Q, WarpState &ws, int w,
                                        int lane, int count, const float4 *s_i, const float4 *s_j,
                                        int32_t *hist_e, int item, int event)
 {
     __syncwarp();
-    bool keep = false;
-    Q1 e;
+    bool keep = false, f64 = false;
+    Q2 out;
+    // the item's slot keeps it until the queue refills after this drain, so the FP64 path
+    // reads it again instead of holding the hits in registers through the fit
+    const int slot = (ws.h1 + lane) & (kRing - 1);
     if (lane < count) {
-        e = Q.q1[w][(ws.h1 + lane) & (kRing - 1)];
+        const Q1 e = Q.q1[w][slot];
+        out.code = e.code;
         const float4 p1 = s_i[code_i(e.code)];
         const float4 p2 = s_j[code_j(e.code)];
         const float4 p3 = make_float4(e.x, e.y, e.z, 0.0f);
         Trans t;
-        const int st = fit_transverse_bound(p1, p2, p3, A.C, t);
-        keep = (st == kNeedFp64) || (st == kPass && z_may_accept(p1, p2, p3, t, A.C));
+        const int st = fit_transverse(p1, p2, p3, A.C, t);
         ws.n_fit++;
+        if (st == kPass) {
+            ws.n_exact++;
+            const int sl = fit_longitudinal(p1, p2, p3, t, A.C, out.cot, out.z0);
+            if (sl == kPass) {
+                keep = true;
+                out.cx = t.cx;
+                out.cy = t.cy;
+                out.sgn = t.sgn;
+                out.qopt = t.qopt;
+                out.d0 = t.d0;
+            } else {
+                f64 = sl == kNeedFp64;
+            }
+        } else {
+            f64 = st == kNeedFp64;
+        }
     }
     ws.h1 = (ws.h1 + count) & (kRing - 1);
     ws.n1 -= count;
+    // FP64 recomputation of the near-collinear / degenerate ones (rare)
+    if (__any_sync(kFull, f64)) {
+        bool has = false;
+        uint32_t bin = 0;
+        if (f64) {
+            const Q1 e = Q.q1[w][slot];
+            const float4 p1 = s_i[code_i(e.code)];
+            const float4 p2 = s_j[code_j(e.code)];
+            const float4 p3 = make_float4(e.x, e.y, e.z, 0.0f);
+            double par[5];
+            has = (fit_f64(p1, p2, p3, A.C, par, bin) == kFit64Accepted);
+            ws.n_fp64++;
+        }
+        __syncwarp();
+        push_votes(A, Q, ws, w, lane, has, bin, out.code, hist_e, item, event);
+    }
     __syncwarp();
     const unsigned m = __ballot_sync(kFull, keep);
     if (keep) {
         const int pos = (ws.h2 + ws.n2 + __popc(m & lanemask_lt())) & (kRing - 1);
-        Q.q2[w][pos] = e;
+        Q.q2[w][pos] = out;
     }
     ws.n2 += __popc(m);
     if (ws.n2 >= kWarp)
-        drain2<NW, TJ>(A, Q, ws, w, lane, kWarp, s_i, s_j, hist_e, item, event);
+        drain2<NW, TJ>(A, Q, ws, w, lane, kWarp, hist_e, item, event);
 }
 
 template <int TI, int TJ, int KC, int MINB>
@@ -268,7 +298,7 @@ __global__ void __launch_bounds__(TI *TJ, MINB) k_vote(VoteArgs A)
         if (ws.n1 > 0)
             drain1<NW, TJ>(A, Q, ws, w, lane, ws.n1, s_i, s_j, hist_e, (int)item, e);
         while (ws.n2 > 0)
-            drain2<NW, TJ>(A, Q, ws, w, lane, min(ws.n2, kWarp), s_i, s_j, hist_e, (int)item, e);
+            drain2<NW, TJ>(A, Q, ws, w, lane, min(ws.n2, kWarp), hist_e, (int)item, e);
         if (ws.ns > 0) {
             __syncwarp();
             flush_votes(A, Q, ws, w, lane, ws.ns, (int)item, e);
@@ -341,7 +371,7 @@ cudaError_t vote_occ(int *blocks)
     cudaError_t vote_dispatch_level##LEVEL(int op, int ti, int tj, const VoteArgs *A,          \
                                            int grid, cudaStream_t s, int *blocks)              \
     {                                                                                          \
-        constexpr int KC = 1024;                                                               \
+        constexpr int KC = 768;                                                                \
         if (ti == 16 && tj == 16)                                                              \
             return op == 0 ? vote_prepare<16, 16, KC, LEVEL>()                                 \
                    : op == 1 ? vote_launch<16, 16, KC, LEVEL>(*A, grid, s)                     \
@@ -362,6 +392,16 @@ cudaError_t vote_occ(int *blocks)
             return op == 0 ? vote_prepare<4, 16, KC, 4 * LEVEL>()                              \
                    : op == 1 ? vote_launch<4, 16, KC, 4 * LEVEL>(*A, grid, s)                  \
                              : vote_occ<4, 16, KC, 4 * LEVEL>(blocks);                         \
+        /* one-warp blocks: no block-wide barrier waits on other warps; 8 LEVEL blocks of */ \
+        /* 32 threads per SM, outer hits staged 128 at a time to fit the shared memory    */ \
+        if (ti == 8 && tj == 4)                                                                \
+            return op == 0 ? vote_prepare<8, 4, 128, 8 * LEVEL>()                              \
+                   : op == 1 ? vote_launch<8, 4, 128, 8 * LEVEL>(*A, grid, s)                  \
+                             : vote_occ<8, 4, 128, 8 * LEVEL>(blocks);                         \
+        if (ti == 4 && tj == 8)                                                                \
+            return op == 0 ? vote_prepare<4, 8, 128, 8 * LEVEL>()                              \
+                   : op == 1 ? vote_launch<4, 8, 128, 8 * LEVEL>(*A, grid, s)                  \
+                             : vote_occ<4, 8, 128, 8 * LEVEL>(blocks);                         \
         return cudaErrorInvalidValue;                                                          \
     }
 

@@ -132,7 +132,7 @@ def test_batch_of_uneven_events(trk):
     _full_compare(trk, cfg, batch)
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 16), (16, 8), (8, 8), (4, 16)])
+@pytest.mark.parametrize("tile", [(16, 16), (8, 16), (16, 8), (8, 8), (4, 16), (8, 4), (4, 8)])
 def test_tile_shapes_agree(trk, tile):
     cfg = ev.load_workload("barrel10_500trk")
     cfg["events"]["n_tracks"] = 30
@@ -285,7 +285,8 @@ def test_autotune_keeps_results(trk):
     rec, res0, hits = _run(trk, cfg, batch)
     offs = torch.from_numpy(batch.offsets).cuda()
     best = rec.autotune(hits, offs, reps=1)
-    assert (best["tile_i"], best["tile_j"]) in [(16, 16), (8, 16), (16, 8), (8, 8), (4, 16)]
+    assert (best["tile_i"], best["tile_j"]) in [(16, 16), (8, 16), (16, 8), (8, 8), (4, 16),
+                                                (8, 4), (4, 8)]
     assert best["vote_level"] in (2, 3, 4) and best["vote_ms"] > 0
     res1 = rec.result(rec.reconstruct_device(hits, offs))
     assert np.array_equal(res0.cand, res1.cand)

