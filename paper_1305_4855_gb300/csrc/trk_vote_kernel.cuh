@@ -47,7 +47,8 @@ struct WarpState {
     int h1, n1, h2, n2, hs, ns;
     int64_t res_chunk;            // next reserved chunk index
     int res_left;                 // reserved chunks left
-    unsigned long long n_fit, n_exact, n_fp64, n_votes;
+    uint32_t n_fit, n_exact, n_fp64, n_votes;   // per lane; below 2^32 for any call
+                                                 // under 6e14 triplets
 };
 
 template <int NW>
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(TI *TJ, MINB) k_vote(VoteArgs A)
         }
     }
     // statistics
-    unsigned long long nf = ws.n_fit, nx = ws.n_exact, n64 = ws.n_fp64;
+    unsigned long long nf = ws.n_fit, nx = ws.n_exact, n64 = ws.n_fp64, nv = ws.n_votes;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         nf += __shfl_xor_sync(kFull, nf, o);
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(TI *TJ, MINB) k_vote(VoteArgs A)
         atomicAdd(&A.ctr->n_exact, nx);
         if (n64)
             atomicAdd(&A.ctr->n_fp64, n64);
-        atomicAdd(&A.ctr->n_votes, ws.n_votes);
+        atomicAdd(&A.ctr->n_votes, nv);
     }
 }
 
