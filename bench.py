@@ -688,11 +688,11 @@ LAUNCHES_PER_CALL = 1 + 1 + 1 + 3 + 9 + 1 + 2 + 1 + 1 + 1
 # only while the vote-kernel sources hash to the recorded digest, and the traffic is
 # reported as null for a tuning without a record.
 VOTE_TRAFFIC = {"workload": "barrel10_500trk",
-                "sources_sha256": "e4aaa436c242db35ebb528e608eab1ca7e0f7bd60532718bbc611dd778550853",
-                "records": [{"tile_i": 16, "tile_j": 8, "vote_level": 4,
-                             "bytes": 1.119124736e9 + 3.09147904e9},
+                "sources_sha256": "eb2709d8e7a920291cd8b6a360cb81f62862d1a0e5e65b135506fa4f15531037",
+                "records": [{"tile_i": 8, "tile_j": 4, "vote_level": 3,
+                             "bytes": 0.97245824e9 + 2.792216064e9},
                             {"tile_i": 8, "tile_j": 4, "vote_level": 4,
-                             "bytes": 1.187623168e9 + 3.198149888e9}]}
+                             "bytes": 1.099234816e9 + 2.996451328e9}]}
 VOTE_SOURCES = ["trk_common.cuh", "trk_vote_kernel.cuh", "trk_vote.cu", "trk_vote_l2.cu",
                 "trk_vote_l3.cu", "trk_vote_l4.cu"]
 

