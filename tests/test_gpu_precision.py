@@ -73,8 +73,6 @@ def test_precision_study_2000trk(trk):
         "acceptance_mismatch_unexplained": int(((acc64 != acc32) & ~ref["amb"]).sum()),
         "fp64_recomputed": int(((flags & 2) != 0).sum()),
         "tolerance_rel": EPS_REL,
-        # the vote kernel's pre-test must keep every triplet the exact fit or the oracle
-        # accepts (outside the edge-ambiguity band)
     }
     print("PRECISION", json.dumps(report))
     assert report["accepted_fp64"] > 100000
