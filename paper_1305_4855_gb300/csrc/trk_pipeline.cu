@@ -468,7 +468,7 @@ __device__ __forceinline__ IntV<V> vcomb(IntV<V> a, const IntV<V> &b)
 }
 
 template <int V>
-__global__ void __launch_bounds__(kPeakThreads, 3) k_peak_pass2(const int32_t *hist, const int32_t *m3,
+__global__ void __launch_bounds__(kPeakThreads, 4) k_peak_pass2(const int32_t *hist, const int32_t *m3,
                                                              FitConst C, int g0, int G,
                                                              int threshold, const int32_t *status,
                                                              uint32_t *cbits, int64_t W,
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(kPeakThreads, 3) k_peak_pass2(const int32_t *h
             };
             // phi0 rows in groups of kR: the column maxima of rows i0+1 .. i0+kR and the
             // counts of rows i0 .. i0+kR-1 are loaded together, then the window slides.
-            constexpr int kR = V == 1 ? 8 : 4;
+            constexpr int kR = V == 1 ? 8 : 2;
             IntV<V> zero;
 #pragma unroll
             for (int c = 0; c < V; ++c)
