@@ -16,6 +16,8 @@ test: it imports neither the oracle nor the CUDA library.
   track_fit_chi2.json -- the candidate fit (Sec. 8 and Fig. 6: candidates are fitted to
       their hits) on hit lists whose fitted circle and line are fixed by symmetry or by
       construction, with their residual sums.
+  hand_bins.json -- acceptance, bin numbers and ambiguity flags of triplets with exact
+      parameters, on a binning with a different count in every dimension.
 
 Run: python tests/golden/make_fixtures.py
 """
@@ -217,7 +219,88 @@ def track_fit_chi2():
                    "per-layer choice keeps (32, 26); the refit and both sums equal B's",
         b_tesla=B, hits=hits_c, layers=[0, 1, 1, 2, 3], used=[1, 1, 0, 1, 1],
         expected=[0.0, -1.0 / (K * B * R), 10.0, 0.5, 1.0], chi2=[0.0, chi2_rz]))
+    # D: a list symmetric under x -> -x.  Layers 0 and 3 hold one hit each on the y axis,
+    # (0, 5) and (0, 55); layers 1 and 2 hold mirror pairs, (+-20, 15) and (+-15, 50).  All six
+    # lie on the circle centre (0, 30), radius 25 (15-20-25 triangles), and the mirror symmetry
+    # puts the all-hit circle's centre on the y axis, so the two hits of a pair are equally far
+    # from it: a tie, which keeps the earlier hit of the list (+20, then +15).  The refit on the
+    # four kept hits is the same circle.  Angles about the centre in layer order: -90, -36.9,
+    # 53.1, 90 degrees, counter-clockwise (negative charge); P = (0, 5), tangent +x: phi0 = 0,
+    # d0 = 5.  z = 0 everywhere: cot = 0, z0 = 0, both sums 0.  amb bit 0: a layer's two
+    # smallest residuals are equal.
+    cases.append(dict(
+        name="tie_keeps_the_earlier_hit",
+        derivation="mirror-symmetric list on the circle centre (0,30), R = 25: equal residuals "
+                   "within each pair, the earlier hit of each pair is kept; phi0 = 0, d0 = 5",
+        b_tesla=B,
+        hits=[[0.0, 5.0, 0.0], [20.0, 15.0, 0.0], [-20.0, 15.0, 0.0], [15.0, 50.0, 0.0],
+              [-15.0, 50.0, 0.0], [0.0, 55.0, 0.0]],
+        layers=[0, 1, 1, 2, 2, 3], used=[1, 1, 0, 1, 0, 1],
+        expected=[0.0, -1.0 / (K * B * 25.0), 5.0, 0.0, 0.0], chi2=[0.0, 0.0], amb=1))
     return dict(source="hand-derived candidate-fit sums, see make_fixtures.py", cases=cases)
+
+
+def hand_bins():
+    """Acceptance, bin numbers and ambiguity flags of triplets whose parameters are exact.
+
+    The hits lie on straight lines parallel to an axis (B = 3.8 T, D = 0 exactly, so q/pT = 0),
+    or on a circle through points of 3-4-5 triangles.  The binning has a different count in
+    every dimension, so a bin number written with the wrong strides differs from the one
+    expected.  Each index below is worked out by hand: the count of whole widths between the
+    lower edge and the value.  Ranges: phi0 [-pi, pi) periodic, q/pT [-1, 1), d0 [-3, 3),
+    cot [-1.25, 1.25), z0 [-20, 20); counts 7, 5, 12, 4, 6; widths 2pi/7, 0.4, 0.5, 0.625,
+    20/3.  Bits of `amb`: 1 a parameter within eps of a bin edge or range limit
+    (eps = 1e-5 max(|p|, half-range)), 2 rejected only by parameters within eps outside
+    their range, 4 a hit at the point of the circle opposite the perigee.
+    """
+    binning = dict(lo=[-math.pi, -1.0, -3.0, -1.25, -20.0], hi=[math.pi, 1.0, 3.0, 1.25, 20.0],
+                   n=[7, 5, 12, 4, 6], periodic=[True, False, False, False, False])
+    # the longitudinal part of every straight case: arcs s = 1, 2, 4 from the perigee and
+    # z = 2 + 0.25 s, so cot = 0.25 (index 2: 1.5/0.625 = 2.4) and z0 = 2 (index 3: 22/(20/3)
+    # = 3.3); phi0 = 0 has index 3 (pi/(2pi/7) = 3.5) and q/pT = 0 index 2 (1/0.4 = 2.5)
+    z = [2.25, 2.5, 3.0]
+    cases = []
+
+    def line(y, sign):
+        return [[sign * 1.0, y, z[0]], [sign * 2.0, y, z[1]], [sign * 4.0, y, z[2]]]
+    cases.append(dict(
+        name="d0_on_its_lower_limit", hits=line(-3.0, 1.0), status=0, idx=[3, 2, 0, 2, 3],
+        amb=1, amb_mask=7,
+        why="moving along +x at y = -3: perigee (0,-3), phi0 = 0, d0 = -3 = lo: accepted in d0 "
+            "bin 0 (the lower limit is inside), and on an edge"))
+    cases.append(dict(
+        name="d0_on_its_upper_limit", hits=line(3.0, 1.0), status=1, idx=None, amb=3,
+        amb_mask=7,
+        why="moving along +x at y = +3: d0 = +3 = hi is outside [lo, hi): rejected, and only by "
+            "a value on its limit"))
+    cases.append(dict(
+        name="phi0_equal_to_pi_wraps", hits=line(1.2, -1.0), status=0, idx=[0, 2, 3, 2, 3],
+        amb=1, amb_mask=7,
+        why="moving along -x at y = 1.2: phi0 = atan2(0, -3) = pi, which the period maps to "
+            "-pi (bin 0); perigee (0, 1.2), d0 = 1.2 cos(pi) = -1.2 (index 3: 1.8/0.5 = 3.6)"))
+    cases.append(dict(
+        name="d0_just_above_the_edge_at_zero", hits=line(1e-6, 1.0), status=0,
+        idx=[3, 2, 6, 2, 3], amb=1, amb_mask=7,
+        why="y = 1e-6: d0 = 1e-6 (index 6), 1e-6 above the edge at 0; eps is 1e-5 times the "
+            "half-range 3, not times |d0|, so the triplet is edge-ambiguous"))
+    cases.append(dict(
+        name="interior", hits=line(-2.2, 1.0), status=0, idx=[3, 2, 1, 2, 3], amb=0,
+        amb_mask=7,
+        why="y = -2.2: d0 = -2.2 (index 1: 0.8/0.5 = 1.6); every value at least 0.1 width "
+            "from an edge: not ambiguous"))
+    cases.append(dict(
+        name="hit_opposite_the_perigee",
+        hits=[[240.0, 81.0, 0.0], [400.0, 401.0, 0.0], [0.0, 801.0, 0.0]], status=0, idx=None,
+        amb=4, amb_mask=4,
+        why="circle centre (0,401), R = 400 through (240,81), (400,401), (0,801); perigee "
+            "(0,1); the third hit is the point opposite it (half-angle asin(1) = pi/2)"))
+    cases.append(dict(
+        name="no_hit_opposite_the_perigee",
+        hits=[[240.0, 81.0, 0.0], [400.0, 401.0, 0.0], [320.0, 641.0, 0.0]], status=0,
+        idx=None, amb=0, amb_mask=4,
+        why="the same circle with the third hit at (320,641), 126.9 degrees from the perigee"))
+    return dict(source="hand-worked binning cases, see make_fixtures.py", b_tesla=B,
+                binning=binning, cases=cases)
 
 
 if __name__ == "__main__":
@@ -229,4 +312,7 @@ if __name__ == "__main__":
         json.dump(bin_centres(), f, indent=1)
     with open(os.path.join(HERE, "track_fit_chi2.json"), "w") as f:
         json.dump(track_fit_chi2(), f, indent=1)
-    print("wrote hand_triplets.json, peak_rule.json, bin_centres.json, track_fit_chi2.json")
+    with open(os.path.join(HERE, "hand_bins.json"), "w") as f:
+        json.dump(hand_bins(), f, indent=1)
+    print("wrote hand_triplets.json, peak_rule.json, bin_centres.json, track_fit_chi2.json, "
+          "hand_bins.json")

@@ -23,6 +23,32 @@ def _setup(kind, n_cols=64, n_rows=32, lo=-8.0, hi=8.0, T=3, b=0.0):
                           b_tesla=b)
 
 
+def test_column_centres_hand_worked():
+    # columns sit at the centres of equal slices of the angle range: two straight columns at
+    # 45 and 135 degrees, four at 22.5, 67.5, 112.5, 157.5; four curved (phi0 over a full
+    # turn) at -135, -45, 45, 135 degrees
+    pi = np.pi
+    assert np.allclose(_setup("straight", n_cols=2).columns(), [pi / 4, 3 * pi / 4], atol=1e-15)
+    assert np.allclose(_setup("straight", n_cols=4).columns(),
+                       [pi / 8, 3 * pi / 8, 5 * pi / 8, 7 * pi / 8], atol=1e-15)
+    assert np.allclose(_setup("curved_ip", n_cols=4, b=3.8).columns(),
+                       [-3 * pi / 4, -pi / 4, pi / 4, 3 * pi / 4], atol=1e-15)
+    # the hit (1, 0) lies on the lines x cos(t) + y sin(t) = rho with rho = cos(t): at 45 and
+    # 135 degrees rho = +-sqrt(2)/2, rows 19 and 4 of 24 rows of width 0.1 from -1.2
+    s = _setup("straight", n_cols=2, n_rows=24, lo=-1.2, hi=1.2)
+    j, _ = H.votes(np.array([[1.0, 0.0]]), s)
+    assert j[0].tolist() == [19, 4]
+
+
+def test_vertex_grid_is_half_open():
+    # a vertical line x = rho (theta = 0) votes once per y row in the x column of rho; the
+    # grid covers [-2, 2) in 5 cells: x = -2 is inside (column 0), x = +2 is outside
+    vs = H.VertexSetup(n_bins=5, range=2.0, threshold=2)
+    inside, outside = H.vertex_votes(np.array([[0.0, -2.0], [0.0, 2.0]]), vs)
+    assert [v[0] for v in inside] == [0, 1, 2, 3, 4]
+    assert outside == []
+
+
 def test_straight_line_points_vote_in_one_bin():
     s = _setup("straight", n_cols=180, n_rows=64, lo=-16.0, hi=16.0)
     rng = np.random.default_rng(1)

@@ -1,6 +1,7 @@
 """Pins of the FP64 oracle against things other than itself (CPU only).
 
   * hand-derived worked triplets (tests/golden/hand_triplets.json);
+  * hand-worked acceptance, bins and ambiguity flags (tests/golden/hand_bins.json);
   * a charged particle integrated through F = q v x B with RK4: the oracle must recover
     the starting perigee from three layer crossings (checks the charge sign and the
     phi0 / d0 conventions against the force law, not against a closed form);
@@ -52,6 +53,27 @@ def test_golden_hand_triplets():
         assert par is not None, c["name"]
         ok, d = _close(par, c["expected"], rel=1e-12, floor=1e-12)
         assert ok, (c["name"], par, c["expected"], d)
+
+
+def test_golden_hand_bins():
+    # acceptance, bin numbers and ambiguity bits of triplets with exact parameters
+    # (tests/golden/hand_bins.json): the half-open ranges, the phi0 period, row-major strides
+    # on a binning with a different count per dimension, eps scaled by the half-range, and the
+    # flag of a hit opposite the perigee
+    g = json.load(open(os.path.join(GOLDEN, "hand_bins.json")))
+    b = g["binning"]
+    s = oracle.OracleSetup(b_tesla=g["b_tesla"], n_layers=3,
+                           triples=np.array([[0, 1, 2]], np.int32), lo=np.array(b["lo"]),
+                           hi=np.array(b["hi"]), n=np.array(b["n"]),
+                           periodic=np.array(b["periodic"]), threshold=2)
+    for c in g["cases"]:
+        f = oracle.fit_list(np.array(c["hits"]), np.array([0, 1, 2], np.int32),
+                            np.array([[0, 1, 2]], np.int32), s)
+        assert int(f["status"][0]) == c["status"], c["name"]
+        if c["idx"] is not None:
+            assert int(f["bin"][0]) == int(np.ravel_multi_index(tuple(c["idx"]), tuple(b["n"]))), \
+                (c["name"], np.unravel_index(int(f["bin"][0]), tuple(b["n"])))
+        assert int(f["amb_bits"][0]) & c["amb_mask"] == c["amb"], (c["name"], f["amb_bits"])
 
 
 def test_golden_hand_triplets_from_float32_hits():
@@ -299,8 +321,10 @@ def _tiny_event(seed, per_layer=5):
 def test_brute_force_agreement(seed):
     cfg, xyz, layer = _tiny_event(seed)
     # a binning wide enough that most combinations vote (stresses the whole range logic)
+    # (a different bin count per dimension, so that wrong row-major strides change the bins)
     s = oracle.OracleSetup.from_workload(cfg, lo=np.array([-math.pi, -3.0, -12.0, -4.0, -60.0]),
-                                         hi=np.array([math.pi, 3.0, 12.0, 4.0, 60.0]))
+                                         hi=np.array([math.pi, 3.0, 12.0, 4.0, 60.0]),
+                                         n=np.array([16, 12, 10, 8, 6]))
     offs = np.array([0, len(xyz)], dtype=np.int64)
     e = oracle.enumerate_batch(xyz, layer, offs, s)
     bf = brute_force.enumerate_event(xyz.astype(np.float64), layer, s.triples, s.b_tesla,
