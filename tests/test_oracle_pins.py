@@ -569,8 +569,10 @@ def test_block_peaks_on_random_histograms():
                                threshold=3)
     n0, n1 = 5, 4
     inner = 3 * 4 * 3
-    for trial in range(20):
-        h = rng.integers(0, 6, size=n0 * n1 * inner)
+    for trial in range(40):
+        # counts up to 5 make plateaus (ties decided by the bin number); counts up to 10^6
+        # make strict maxima in every row, so that the neighbours across the phi0 wrap decide
+        h = rng.integers(0, 6 if trial % 2 == 0 else 1_000_000, size=n0 * n1 * inner)
         ub = np.nonzero(h)[0]
         keep = [(int(rng.integers(0, n0)), int(rng.integers(0, n1))) for _ in range(3)]
         keep = sorted(set(keep))
