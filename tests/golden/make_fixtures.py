@@ -190,7 +190,10 @@ def track_fit_chi2():
         b_tesla=B, hits=[[0.0, 9.5, 3.0], [39.5, 50.0, 3.0], [0.0, 90.5, 3.0], [-39.5, 50.0, 3.0]],
         layers=[0, 1, 2, 3], used=[1, 1, 1, 1],
         expected=[0.0, -1.0 / (K * B * rp), 50.0 - rp, 0.0, 3.0],
-        chi2=[2.0 * (40.5 - rp) ** 2 + 2.0 * (39.5 - rp) ** 2, 0.0]))
+        chi2=[2.0 * (40.5 - rp) ** 2 + 2.0 * (39.5 - rp) ** 2, 0.0],
+        amb=4, amb_why="(0, 90.5) lies on the line from the perigee through the centre, "
+                       "beyond it: the point opposite the perigee (bit 4); one hit per layer, "
+                       "so no selection tie"))
     # B: four hits exactly on the circle centre (0, 50), radius 40 (3-4-5 triangles); the
     # arcs from P = (0, 10) are 40 (theta + pi/2).  z = 1 + 0.5 s + r with
     # r = 0.01 (s3 - s2, s1 - s3, s2 - s1, 0), orthogonal to (1,1,1,1) and to s, so the
@@ -209,7 +212,8 @@ def track_fit_chi2():
                    "z residuals orthogonal to 1 and s: the line is z = 1 + 0.5 s; "
                    "chi2_rz = sum r_k^2, chi2_rphi = 0",
         b_tesla=B, hits=hits, layers=[0, 1, 2, 3], used=[1, 1, 1, 1],
-        expected=[0.0, -1.0 / (K * B * R), 10.0, 0.5, 1.0], chi2=[0.0, chi2_rz]))
+        expected=[0.0, -1.0 / (K * B * R), 10.0, 0.5, 1.0], chi2=[0.0, chi2_rz],
+        amb=0, amb_why="angles from the perigee at most 143 degrees; one hit per layer"))
     # C: B plus a second layer-1 hit far off the circle; it is dropped, and the sums run
     # over the kept hits only, so chi2 equals B's.
     hits_c = hits[:2] + [[32.0, 35.0, 0.0]] + hits[2:]
@@ -218,7 +222,8 @@ def track_fit_chi2():
         derivation="B with an extra layer-1 hit (32, 35), 4.7 cm inside the circle: the "
                    "per-layer choice keeps (32, 26); the refit and both sums equal B's",
         b_tesla=B, hits=hits_c, layers=[0, 1, 1, 2, 3], used=[1, 1, 0, 1, 1],
-        expected=[0.0, -1.0 / (K * B * R), 10.0, 0.5, 1.0], chi2=[0.0, chi2_rz]))
+        expected=[0.0, -1.0 / (K * B * R), 10.0, 0.5, 1.0], chi2=[0.0, chi2_rz],
+        amb=0, amb_why="the layer-1 residuals differ by about 4.7 cm: no tie"))
     # D: a list symmetric under x -> -x.  Layers 0 and 3 hold one hit each on the y axis,
     # (0, 5) and (0, 55); layers 1 and 2 hold mirror pairs, (+-20, 15) and (+-15, 50).  All six
     # lie on the circle centre (0, 30), radius 25 (15-20-25 triangles), and the mirror symmetry
@@ -227,7 +232,7 @@ def track_fit_chi2():
     # four kept hits is the same circle.  Angles about the centre in layer order: -90, -36.9,
     # 53.1, 90 degrees, counter-clockwise (negative charge); P = (0, 5), tangent +x: phi0 = 0,
     # d0 = 5.  z = 0 everywhere: cot = 0, z0 = 0, both sums 0.  amb bit 0: a layer's two
-    # smallest residuals are equal.
+    # smallest residuals are equal; bit 4: (0, 55) is the point opposite the perigee.
     cases.append(dict(
         name="tie_keeps_the_earlier_hit",
         derivation="mirror-symmetric list on the circle centre (0,30), R = 25: equal residuals "
@@ -236,7 +241,8 @@ def track_fit_chi2():
         hits=[[0.0, 5.0, 0.0], [20.0, 15.0, 0.0], [-20.0, 15.0, 0.0], [15.0, 50.0, 0.0],
               [-15.0, 50.0, 0.0], [0.0, 55.0, 0.0]],
         layers=[0, 1, 1, 2, 2, 3], used=[1, 1, 0, 1, 0, 1],
-        expected=[0.0, -1.0 / (K * B * 25.0), 5.0, 0.0, 0.0], chi2=[0.0, 0.0], amb=1))
+        expected=[0.0, -1.0 / (K * B * 25.0), 5.0, 0.0, 0.0], chi2=[0.0, 0.0], amb=5,
+        amb_why="equal residuals in layers 1 and 2 (bit 1); (0, 55) opposite the perigee (bit 4)"))
     return dict(source="hand-derived candidate-fit sums, see make_fixtures.py", cases=cases)
 
 

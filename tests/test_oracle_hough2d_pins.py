@@ -40,6 +40,45 @@ def test_column_centres_hand_worked():
     assert j[0].tolist() == [19, 4]
 
 
+def test_single_column_rows_edges_and_centres():
+    # one straight column sits at 90 degrees, where the row value of a hit (0, y) is y
+    # itself: rows of width 0.5 over [-1, 1).  y = 0.5 is on the edge between rows 2 and 3
+    # (ambiguous), y = 0.3 is inside row 2, y = -1 is the first row, y = 1 is outside.
+    s = _setup("straight", n_cols=1, n_rows=4, lo=-1.0, hi=1.0, T=2)
+    j, amb = H.votes(np.array([[0.0, 0.5], [0.0, 0.3], [0.0, -1.0], [0.0, 1.0]]), s)
+    assert j[:, 0].tolist() == [3, 2, 0, -1]
+    assert amb[:, 0].tolist() == [True, False, True, True]
+    # three hits on the line y = 0.3 vote in row 2, whose centre is -1 + 2.5 * 0.5 = 0.25
+    ev = H.reconstruct(np.array([[0.0, 0.3], [5.0, 0.3], [-5.0, 0.3]]), np.array([0, 3]), s)[0]
+    assert ev["cand_bins"].tolist() == [2] and ev["cand_votes"].tolist() == [3]
+    assert np.allclose(ev["cand_params"], [[np.pi / 2, 0.25]], atol=1e-15)
+    assert ev["cand_hits"][0].tolist() == [0, 1, 2]
+
+
+def test_vertex_raster_and_centre_hand_worked():
+    vs = H.VertexSetup(n_bins=4, range=2.0, threshold=2)
+    # the line through the origin at 60 degrees, y = -x / sqrt(3), is rastered along x
+    # (|sin| >= |cos|): at the column centres -1.5, -0.5, 0.5, 1.5 it has y = 0.87, 0.29,
+    # -0.29, -0.87, rows 2, 2, 1, 1: cells 0*4+2, 1*4+2, 2*4+1, 3*4+1
+    cells = [v[0] for v in H.vertex_votes(np.array([[np.pi / 3, 0.0]]), vs)[0]]
+    assert cells == [2, 6, 9, 13]
+    # the vertical line x = 1.5 and the horizontal line y = -0.5 meet in cell (3, 1), whose
+    # centre is (1.5, -0.5)
+    r = H.vertex_hough(np.array([[0.0, 1.5], [np.pi / 2, -0.5]]), vs)
+    assert r["cells"].tolist() == [13] and r["votes"].tolist() == [2]
+    assert np.allclose(r["centres"], [[1.5, -0.5]])
+    assert r["tracks"][0].tolist() == [0, 1]
+
+
+def test_vertex_minimum_votes_is_inclusive():
+    # candidates with exactly min_track_votes votes draw their lines; fewer do not
+    vs = H.VertexSetup(n_bins=4, range=2.0, threshold=2, min_track_votes=3)
+    event = dict(cand_votes=np.array([3, 2, 3]),
+                 cand_params=np.array([[0.0, 1.5], [np.pi / 3, 0.0], [np.pi / 2, -0.5]]))
+    r = H.event_vertices(event, vs)
+    assert r["cells"].tolist() == [13] and r["tracks"][0].tolist() == [0, 2]
+
+
 def test_vertex_grid_is_half_open():
     # a vertical line x = rho (theta = 0) votes once per y row in the x column of rho; the
     # grid covers [-2, 2) in 5 cells: x = -2 is inside (column 0), x = +2 is outside

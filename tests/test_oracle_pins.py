@@ -422,6 +422,24 @@ def test_invalid_layer_is_rejected():
         oracle.enumerate_batch(b.xyz, lay, b.offsets, s)
 
 
+def test_degenerate_triplets_are_counted():
+    # (10,0), (0,10), (-10,0) and (10,0), (0,10), (0,-10) lie on the circle of radius 10 about
+    # the origin: a centre on the origin has no perigee, so both triplets are degenerate;
+    # (10,0), (0,10), (5,30) is an ordinary circle.  The full and the block-restricted
+    # enumerations both count exactly two.
+    xyz = np.array([[10.0, 0.0, 0.0], [0.0, 10.0, 1.0], [-10.0, 0.0, 2.0], [0.0, -10.0, 2.0],
+                    [5.0, 30.0, 3.0]])
+    layer = np.array([0, 1, 2, 2, 2], np.int32)
+    s = oracle.OracleSetup(b_tesla=3.8, n_layers=3, triples=np.array([[0, 1, 2]], np.int32),
+                           lo=np.array([-math.pi, -2.0, -50.0, -5.5, -30.0]),
+                           hi=np.array([math.pi, 2.0, 50.0, 5.5, 30.0]), n=np.array([4, 3, 2, 2, 2]),
+                           periodic=np.array([True, False, False, False, False]), threshold=2)
+    full = oracle.enumerate_batch(xyz, layer, np.array([0, 5], np.int64), s)
+    assert full["n_triplets"] == 3 and full["n_degenerate"] == 2
+    blk = oracle.enumerate_blocks(xyz, layer, s, [(0, 0)], [], [])
+    assert blk["n_triplets"] == 3 and blk["n_degenerate"] == 2
+
+
 def test_fit_list_matches_enumeration():
     cfg, b, s = _c1()
     e = oracle.enumerate_batch(b.xyz, b.layer, b.offsets, s)
